@@ -1,0 +1,231 @@
+/*
+ * mmc.h -- C ABI of the GB300 (sm_103a) Multipolynomial Monte Carlo library.
+ *
+ * The library estimates Tr(Theta M^-1) for the Wilson-Dirac matrix M with the
+ * multipolynomial Monte Carlo method of Lashomb, Morgan, Whyte and Wilcox,
+ * "Multipolynomial Monte Carlo Trace Estimation" (Lattice 2023):
+ *   Sec. 1 (Eq. 1)  the trace and Hutchinson's Z(4)-noise estimator,
+ *   Sec. 2 (Eq. 2)  the subtracted estimator,
+ *   Sec. 3          GMRES polynomials from Leja-ordered harmonic Ritz values,
+ *   Sec. 5          double (composite) polynomials,
+ *   Sec. 6          the multilevel telescoping sum and exact (probed) last level,
+ *   Sec. 7          deflation of the Monte Carlo levels,
+ *   Sec. 8          deflated solves and the acceptance rules for eigenpairs.
+ *
+ * Conventions shared by every call
+ *   - Every call returns MMC_OK (0) or a negative MMC_ERR_* code; nothing
+ *     aborts or exits.  mmc_last_error() gives a context-owned message.
+ *   - Host arrays are owned by the caller; the library copies what it keeps.
+ *   - Device fields are owned by the caller (e.g. torch tensors) and passed as
+ *     raw device pointers; the library never frees caller memory.  Internal
+ *     work buffers are owned by the context and freed by mmc_destroy().
+ *   - Complex numbers are interleaved (re, im) pairs everywhere.
+ *   - Lattice: dims = {Lx, Ly, Lz, Lt}; site index s = x + Lx(y + Ly(z + Lz t)).
+ *     Canonical host order of a spinor batch: [rhs][t][z][y][x][spin][colour]
+ *     complex128; of the gauge field: [mu][t][z][y][x][row][col] complex128,
+ *     mu = 0:x, 1:y, 2:z, 3:t.
+ *   - Device field layout ("blocked"): [rb][site][c][R] complex, c = 3*spin +
+ *     colour, R = mmc_rhs_block(nrhs) right-hand sides per block, rb = 0 ..
+ *     ceil(nrhs/R)-1; padding RHS slots are kept at zero.  Storage type per
+ *     precision: MMC_F64 complex double (16 B), MMC_F32 complex float (8 B),
+ *     MMC_BF16 two bfloat16 (4 B).  mmc_field_bytes() gives the size.
+ *   - Precision: MMC_F64 computes in FP64; MMC_F32 and MMC_BF16 compute in
+ *     FP32 (BF16 is storage only) and accumulate bilinears in FP64.
+ *   - Calls taking a cudaStream_t (passed as void*) are asynchronous on that
+ *     stream; all others synchronise the context's stream before returning.
+ *   - Dirac matrices: chiral basis, gamma_k = [[0,-i s_k],[i s_k,0]],
+ *     gamma_4 = [[0,1],[1,0]], gamma_5 = diag(1,1,-1,-1).
+ *   - M psi(x) = psi(x) - kappa sum_mu [(1-gamma_mu) U_mu(x) psi(x+mu)
+ *                                     + (1+gamma_mu) U_mu(x-mu)^+ psi(x-mu)],
+ *     periodic in space, antiperiodic in time when requested.
+ *   - Z(4) noise: Philox4x32-10, key (seed mod 2^32, seed >> 32), counter
+ *     (site, noise index, level id, tag); spin-colour component c of the site
+ *     takes i^((w0 >> 2c) & 3) with w0 the first output word.
+ */
+#ifndef MMC_H
+#define MMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mmc_ctx mmc_ctx;
+
+enum {
+  MMC_OK = 0,
+  MMC_ERR_ARG = -1,        /* invalid argument (null pointer, size, handle) */
+  MMC_ERR_NOMEM = -2,      /* device or host allocation failed */
+  MMC_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+  MMC_ERR_BREAKDOWN = -4,  /* Arnoldi breakdown (h_{j+1,j} ~ 0) */
+  MMC_ERR_NOCONV = -5,     /* a solve or eigen iteration did not converge */
+  MMC_ERR_TIMEOUT = -6,    /* a bounded device wait gave up */
+  MMC_ERR_NAN = -7,        /* a NaN or Inf appeared */
+  MMC_ERR_STATE = -8       /* call out of order (e.g. no gauge field loaded) */
+};
+
+enum { MMC_F64 = 0, MMC_F32 = 1, MMC_BF16 = 2 };
+enum { MMC_THETA_ONE = 0, MMC_THETA_G4 = 1, MMC_THETA_G5 = 2 };
+enum { MMC_EXACT_UNIT = 0, MMC_EXACT_PROBE = 1 };
+
+#define MMC_OP_M (-1)   /* operator argument: M itself */
+#define MMC_ZERO (-1)   /* level argument: the zero map */
+#define MMC_INV (-2)    /* level argument: M^-1 (deflated, refined solves) */
+
+#define MMC_TAG_NOISE 0x4E4F4953u   /* 'NOIS': Monte Carlo noise */
+#define MMC_TAG_GMRES 0x474D5253u   /* 'GMRS': GMRES-polynomial start vector */
+#define MMC_TAG_ARNOLDI 0x4445464Cu /* 'DEFL': PP-Arnoldi start vector */
+
+/* Statistics of one Monte Carlo level (Sec. 4, Sec. 6, Sec. 8).
+ * Samples x_j = eta_j^H Theta (A_hi - A_lo) eta_j minus the deflated part;
+ * var_* are unbiased sample variances, stderr_* = sqrt(var/n);
+ * corr = sum_i c_i u_i^H Theta z_i is the exact trace of the deflated part
+ * (zero without deflation); value = mean + corr is the level's estimate. */
+typedef struct {
+  int n;
+  int k_deflated;
+  double mean_re, mean_im;
+  double var_re, var_im, cvar;
+  double stderr_re, stderr_im;
+  double corr_re, corr_im;
+  double value_re, value_im;
+  double seconds;
+  long long matvecs;       /* single-vector applications of M spent */
+} mmc_level_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` for a lattice dims[4] = {Lx,Ly,Lz,Lt}
+ * (each >= 2) and a noise seed (Sec. 1: Z(4) noise).  *ctx is set on success. */
+int mmc_create(mmc_ctx** ctx, const int dims[4], uint64_t seed, int device);
+/* Free every device and host resource of the context.  NULL is accepted. */
+int mmc_destroy(mmc_ctx* ctx);
+/* Message describing the last error of this context (never NULL). */
+const char* mmc_last_error(const mmc_ctx* ctx);
+/* Noise seed of the context; may be changed between calls. */
+int mmc_set_seed(mmc_ctx* ctx, uint64_t seed);
+
+/* RHS block R used for a batch of nrhs vectors (power of two, <= 16). */
+int mmc_rhs_block(int nrhs);
+/* Bytes of a device field of nrhs vectors in precision prec (blocked layout). */
+size_t mmc_field_bytes(const mmc_ctx* ctx, int nrhs, int prec);
+
+/* ------------------------------------------------------------- operator */
+
+/* Load the gauge field (host, canonical complex128 [4][t][z][y][x][3][3]) and the
+ * hopping parameter kappa (Sec. 4); t_antiperiodic != 0 selects antiperiodic time.
+ * Keeps FP64 and FP32 device copies.  Invalidates polynomials and eigenpairs. */
+int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiodic);
+
+/* Convert nrhs host vectors (canonical order, complex128, rhs outermost) into a
+ * device field of precision prec (blocked layout), and back.  Synchronous. */
+int mmc_pack(mmc_ctx* ctx, const double* host, int nrhs, int prec, void* field);
+int mmc_unpack(mmc_ctx* ctx, const void* field, int nrhs, int prec, double* host);
+
+/* y = M x (dagger = 0) or y = M^+ x (dagger = 1) for nrhs vectors of precision
+ * prec (Sec. 1, Eq. 1's Wilson-Dirac matrix).  x and y must not overlap. */
+int mmc_apply_M(mmc_ctx* ctx, const void* x, void* y, int nrhs, int prec, int dagger,
+                void* stream);
+
+/* Fill a field with nrhs Z(4) noise vectors: vector r has noise index first + r,
+ * level id `level` and tag `tag` (Sec. 1, "Z(4) noise"). */
+int mmc_noise(mmc_ctx* ctx, uint32_t level, uint32_t first, uint32_t tag, int nrhs, int prec,
+              void* field, void* stream);
+
+/* ----------------------------------------------------------- polynomials */
+
+/* One GMRES(m) cycle (Sec. 3) of op (MMC_OP_M, or phi_h(M) = M p_h(M) for a single
+ * polynomial handle h) from the normalised Z(4) start vector (noise index 0, level
+ * 0, tag MMC_TAG_GMRES), Arnoldi with CGS2 in FP64 on the device; harmonic Ritz
+ * values and Leja ordering in FP64 on the host.  theta_out (2m doubles, may be
+ * NULL) receives the Leja-ordered values; *handle the new polynomial
+ * (MMC_OP_M: p of degree m-1 in M; else p_out in phi_h(M)). */
+int mmc_gmres_poly(mmc_ctx* ctx, int m, int op_handle, double* theta_out, int* handle);
+
+/* Register a polynomial given by m Leja-ordered roots theta (2m doubles), p of
+ * degree m-1 with pi(a) = prod (1 - a/theta_i) = 1 - a p(a) (Sec. 3). */
+int mmc_poly_from_roots(mmc_ctx* ctx, int m, const double* theta, int* handle);
+
+/* Compose the double polynomial p_double(M) = p_in(M) p_out(phi_in(M)) (Sec. 5)
+ * from a single polynomial h_in in M and a polynomial h_out in phi_in(M). */
+int mmc_poly_double(mmc_ctx* ctx, int h_in, int h_out, int* handle);
+
+/* Number of M applications one vector needs for p_h (degree of p_h). */
+int mmc_poly_degree(const mmc_ctx* ctx, int handle);
+
+/* Scalar values p_h(alpha_j) for n complex points (2n doubles in and out). */
+int mmc_poly_eval(const mmc_ctx* ctx, int handle, int n, const double* alpha, double* out);
+
+/* y = p_h(M) x for nrhs vectors of precision prec (Sec. 3, Sec. 5): the Leja
+ * recurrence, one fused stencil+update kernel per degree.  x, y must differ. */
+int mmc_apply_poly(mmc_ctx* ctx, int handle, const void* x, void* y, int nrhs, int prec,
+                   void* stream);
+
+/* ------------------------------------------------------------- deflation */
+
+/* PP-Arnoldi (Sec. 7): m_arnoldi FP64 Arnoldi steps on phi_h(M) = M p_h(M)
+ * (poly_handle a single polynomial; MMC_OP_M for M itself) from a Z(4) start
+ * vector (tag MMC_TAG_ARNOLDI); every Ritz vector z of phi is tested against M
+ * (lambda = z^H M z, accepted if ||M z - lambda z|| < tol_accept, Sec. 8: 1e-3);
+ * the accepted ones of smallest |lambda|, at most k, are kept with left vectors
+ * u_i = gamma5 z_j (lambda_j = conj lambda_i; |Im| < 2e-4 counts as real) and
+ * U^H Z = I.  lambda_out (2k doubles, may be NULL) receives the eigenvalues. */
+int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arnoldi, double tol_accept,
+                double* lambda_out, int* k_accepted);
+
+/* ---------------------------------------------------------------- solves */
+
+/* Solve M x = b for nrhs FP64 fields (Sec. 1: the solves of Hutchinson's method;
+ * Sec. 8: deflated, polynomial-preconditioned GMRES).  Outer loop in FP64:
+ * r = b - M x, deflated correction x += Z Lambda^-1 U^H r, stop when
+ * ||r|| <= rel_tol ||b|| per vector; inner right-preconditioned FGMRES(m_inner)
+ * in precision prec_inner (MMC_F32 or MMC_BF16 storage, FP32 arithmetic) with
+ * preconditioner p_h(M) (precond_handle, or MMC_ZERO for none).  x is the
+ * initial guess on entry.  *iters receives inner iterations, relres_out (nrhs,
+ * may be NULL) the final relative residuals. */
+int mmc_solve(mmc_ctx* ctx, const void* b, void* x, int nrhs, double rel_tol, int precond_handle,
+              int prec_inner, int m_inner, int max_outer, int* iters, double* relres_out);
+
+/* ----------------------------------------------------------- estimators */
+
+/* One Monte Carlo level (Eq. 2, Sec. 6): n_noise Z(4) vectors (noise indices
+ * first_noise.., level id `level`), samples eta^H Theta (A_hi - A_lo) eta with
+ * hi in {MMC_INV, polynomial handle}, lo in {polynomial handle, MMC_ZERO}.
+ * deflate != 0 (both polynomial) subtracts sum_i c_i (eta^H Theta z_i)(u_i^H eta)
+ * with c_i = p_hi(lambda_i) - p_lo(lambda_i) and reports the exact correction
+ * (Sec. 7).  prec: storage of the polynomial chains.  For hi = MMC_INV the
+ * solves use rel_tol 1e-10, preconditioner `precond` and FGMRES(48).
+ * samples_out (2 n_noise doubles, may be NULL) receives the samples. */
+int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int n_noise,
+                    uint32_t first_noise, uint32_t level, int prec, int precond,
+                    mmc_level_stats* out, double* samples_out);
+
+/* Exact Tr(Theta p_h(M)) (Sec. 6, last level): method MMC_EXACT_UNIT sums all 12V
+ * unit vectors; MMC_EXACT_PROBE uses a site colouring whose equal-colour sites are
+ * farther apart (periodic L1) than the degree of p_h, 12 probe vectors per colour.
+ * out[2] receives the complex trace. */
+int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec, double* out);
+
+/* Number of colours of the probing colouring chosen for a reach (L1 distance). */
+int mmc_probe_colours(mmc_ctx* ctx, int reach, int* n_colours);
+
+/* ---------------------------------------------------- host-only helpers */
+
+/* Harmonic Ritz values of a GMRES(m) cycle (Sec. 3) from its (m+1) x m Hessenberg
+ * matrix H (complex, column-major, leading dimension ldh >= m+1), Leja ordered
+ * into theta_out (2m doubles).  Pure host FP64. */
+int mmc_harmonic_ritz(int m, const double* H, int ldh, double* theta_out);
+/* Leja ordering (Sec. 3) of m complex points: first the largest modulus, then
+ * the maximiser of the product of distances (sum of logs), ties to lowest index. */
+int mmc_leja_order(int m, const double* theta_in, double* theta_out);
+/* Eigenvalues (and right eigenvectors, column-major, if vr != NULL) of a complex
+ * n x n matrix A (column-major, lda >= n); pure host FP64 (Hessenberg reduction
+ * + shifted QR).  Used for the Ritz values of Sec. 3 and Sec. 7. */
+int mmc_eig(int n, const double* A, int lda, double* w, double* vr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMC_H */

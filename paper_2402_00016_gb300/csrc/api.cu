@@ -1,0 +1,306 @@
+// Host side of the C ABI declared in include/mmc.h: the context, the
+// polynomial programs (Sec. 3, Sec. 5) turned into sequences of fused step
+// launches, the CGS2 Arnoldi process (Sec. 3, Sec. 7), deflation (Sec. 7,
+// Sec. 8), the refined deflated solves (Sec. 1, Sec. 8) and the Monte Carlo
+// levels (Eq. 2, Sec. 6, Sec. 7).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mmc::host;
+using mmc::cd;
+using mmc::CMat;
+using mmc::geom;
+
+// =====================================================================  C ABI
+extern "C" {
+
+int mmc_rhs_block(int nrhs) { return nrhs < 1 ? 1 : rhs_block(nrhs); }
+
+size_t mmc_field_bytes(const mmc_ctx* ctx, int nrhs, int prec) {
+  if (!ctx || nrhs < 1 || prec < 0 || prec > 2) return 0;
+  return field_bytes(make_geom(ctx, nrhs), prec);
+}
+
+int mmc_create(mmc_ctx** out, const int dims[4], uint64_t seed, int device) {
+  if (!out || !dims) return MMC_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2) return MMC_ERR_ARG;
+  mmc_ctx* ctx = new (std::nothrow) mmc_ctx();
+  if (!ctx) return MMC_ERR_NOMEM;
+  for (int i = 0; i < 4; ++i) ctx->dims[i] = dims[i];
+  ctx->V = dims[0] * dims[1] * dims[2] * dims[3];
+  ctx->seed = seed;
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  // a blocking stream: ordered with work on the legacy default stream (where torch allocates by default)
+  if (e == cudaSuccess) e = cudaStreamCreate(&ctx->stream);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return MMC_ERR_CUDA;
+  }
+  *out = ctx;
+  return MMC_OK;
+}
+
+int mmc_destroy(mmc_ctx* ctx) {
+  if (!ctx) return MMC_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->scratch)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (ctx->links64) cudaFree(ctx->links64);
+  if (ctx->links32) cudaFree(ctx->links32);
+  if (ctx->Z) cudaFree(ctx->Z);
+  if (ctx->U) cudaFree(ctx->U);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return MMC_OK;
+}
+
+const char* mmc_last_error(const mmc_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+int mmc_set_seed(mmc_ctx* ctx, uint64_t seed) {
+  if (!ctx) return MMC_ERR_ARG;
+  ctx->seed = seed;
+  return MMC_OK;
+}
+
+int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiodic) {
+  if (!ctx || !U) return MMC_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  const int V = ctx->V;
+  // canonical [mu][site][3][3] -> device [site][mu][9] (FP64) and [site][mu][10] (FP32, padded)
+  std::vector<double2> h64(size_t(V) * 4 * 9);
+  std::vector<float2> h32(size_t(V) * 4 * 10, make_float2(0.f, 0.f));
+  for (int mu = 0; mu < 4; ++mu)
+    for (int s = 0; s < V; ++s)
+      for (int k = 0; k < 9; ++k) {
+        size_t src = ((size_t(mu) * V + s) * 9 + k) * 2;
+        double re = U[src], im = U[src + 1];
+        h64[(size_t(s) * 4 + mu) * 9 + k] = make_double2(re, im);
+        h32[(size_t(s) * 4 + mu) * 10 + k] = make_float2(float(re), float(im));
+      }
+  if (!ctx->links64) CK(cudaMalloc(&ctx->links64, h64.size() * sizeof(double2)));
+  if (!ctx->links32) CK(cudaMalloc(&ctx->links32, h32.size() * sizeof(float2)));
+  CK(cudaMemcpy(ctx->links64, h64.data(), h64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->links32, h32.data(), h32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  ctx->kappa = kappa;
+  ctx->tap = t_antiperiodic ? 1 : 0;
+  ctx->gauge = true;
+  ctx->polys.clear();
+  ctx->k_defl = 0;
+  ctx->lambda.clear();
+  return MMC_OK;
+}
+
+int mmc_pack(mmc_ctx* ctx, const double* host, int nrhs, int prec, void* field) {
+  if (!ctx || !host || !field || nrhs < 1 || prec < 0 || prec > 2) return MMC_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  geom g = make_geom(ctx, nrhs);
+  void* canon;
+  const size_t bytes = size_t(nrhs) * ctx->V * 12 * sizeof(double2);
+  TRY(scratch(ctx, "canon", bytes, &canon));
+  CK(cudaMemcpyAsync(canon, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(mmc::launch_pack(prec, g, nrhs, (const double2*)canon, field, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MMC_OK;
+}
+
+int mmc_unpack(mmc_ctx* ctx, const void* field, int nrhs, int prec, double* host) {
+  if (!ctx || !host || !field || nrhs < 1 || prec < 0 || prec > 2) return MMC_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  geom g = make_geom(ctx, nrhs);
+  void* canon;
+  const size_t bytes = size_t(nrhs) * ctx->V * 12 * sizeof(double2);
+  TRY(scratch(ctx, "canon", bytes, &canon));
+  CK(mmc::launch_unpack(prec, g, nrhs, field, (double2*)canon, ctx->stream));
+  CK(cudaMemcpyAsync(host, canon, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MMC_OK;
+}
+
+int mmc_apply_M(mmc_ctx* ctx, const void* x, void* y, int nrhs, int prec, int dagger, void* stream) {
+  TRY(check_ctx(ctx));
+  if (!x || !y || x == y || nrhs < 1 || prec < 0 || prec > 2) RET(MMC_ERR_ARG, "mmc_apply_M: bad argument");
+  return apply_M_impl(ctx, x, y, nrhs, prec, dagger != 0, (cudaStream_t)stream);
+}
+
+int mmc_noise(mmc_ctx* ctx, uint32_t level, uint32_t first, uint32_t tag, int nrhs, int prec, void* field,
+              void* stream) {
+  if (!ctx || !field || nrhs < 1 || prec < 0 || prec > 2) return MMC_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  geom g = make_geom(ctx, nrhs);
+  std::vector<uint2> ids(g.npad);
+  for (int r = 0; r < g.npad; ++r) ids[r] = r < nrhs ? make_uint2(level, first + r) : make_uint2(0xffffffffu, 0);
+  void* dids;
+  TRY(scratch(ctx, "ids", ids.size() * sizeof(uint2), &dids));
+  CK(cudaMemcpyAsync(dids, ids.data(), ids.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+  CK(mmc::launch_noise(prec, g, (const uint2*)dids, tag, ctx->seed, field, nullptr, s));
+  CK(cudaStreamSynchronize(s));  // ids buffer is reused by the next call
+  return MMC_OK;
+}
+
+int mmc_poly_from_roots(mmc_ctx* ctx, int m, const double* theta, int* handle) {
+  if (!ctx || m < 1 || !theta || !handle) return MMC_ERR_ARG;
+  Poly P;
+  P.kind = 0;
+  for (int i = 0; i < m; ++i) {
+    P.theta.push_back(cd(theta[2 * i], theta[2 * i + 1]));
+    if (P.theta.back() == cd(0, 0)) RET(MMC_ERR_ARG, "zero root");
+  }
+  ctx->polys.push_back(P);
+  *handle = int(ctx->polys.size()) - 1;
+  return MMC_OK;
+}
+
+int mmc_poly_double(mmc_ctx* ctx, int h_in, int h_out, int* handle) {
+  if (!ctx || !handle || !valid_poly(ctx, h_in) || !valid_poly(ctx, h_out)) return MMC_ERR_ARG;
+  const Poly &Pi = ctx->polys[h_in], &Po = ctx->polys[h_out];
+  if (Pi.kind != 0 || Pi.op != MMC_OP_M || Po.kind != 0) RET(MMC_ERR_ARG, "mmc_poly_double: needs single polynomials");
+  Poly P;
+  P.kind = 1;
+  P.h_in = h_in;
+  P.h_out = h_out;
+  ctx->polys.push_back(P);
+  *handle = int(ctx->polys.size()) - 1;
+  return MMC_OK;
+}
+
+int mmc_poly_degree(const mmc_ctx* ctx, int handle) {
+  if (!ctx || !valid_poly(ctx, handle)) return MMC_ERR_ARG;
+  return poly_degree(ctx, handle);
+}
+
+int mmc_poly_eval(const mmc_ctx* ctx, int handle, int n, const double* alpha, double* out) {
+  if (!ctx || !valid_poly(ctx, handle) || n < 0 || (n && (!alpha || !out))) return MMC_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    cd v = poly_value(ctx, handle, cd(alpha[2 * i], alpha[2 * i + 1]));
+    out[2 * i] = v.real();
+    out[2 * i + 1] = v.imag();
+  }
+  return MMC_OK;
+}
+
+int mmc_apply_poly(mmc_ctx* ctx, int handle, const void* x, void* y, int nrhs, int prec, void* stream) {
+  TRY(check_ctx(ctx));
+  if (!valid_poly(ctx, handle) || !x || !y || x == y || nrhs < 1 || prec < 0 || prec > 2)
+    RET(MMC_ERR_ARG, "mmc_apply_poly: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  Run base;
+  base.g = make_geom(ctx, nrhs);
+  base.prec = prec;
+  if (prec == MMC_BF16) {
+    void* Y;
+    TRY(scratch(ctx, "yacc", size_t(base.g.npad) * ctx->V * 12 * 8, &Y));
+    TRY(apply_poly_impl(ctx, handle, x, nrhs, prec, ACC_Y, Y, base, s));
+    CK(mmc::launch_convert(MMC_BF16, y, MMC_F32, Y, base.g, s));
+    return MMC_OK;
+  }
+  return apply_poly_impl(ctx, handle, x, nrhs, prec, ACC_Y, y, base, s);
+}
+
+int mmc_gmres_poly(mmc_ctx* ctx, int m, int op_handle, double* theta_out, int* handle) {
+  TRY(check_ctx(ctx));
+  if (m < 1 || !handle) RET(MMC_ERR_ARG, "mmc_gmres_poly: bad argument");
+  if (op_handle != MMC_OP_M) {
+    if (!valid_poly(ctx, op_handle) || ctx->polys[op_handle].kind != 0 || ctx->polys[op_handle].op != MMC_OP_M)
+      RET(MMC_ERR_ARG, "mmc_gmres_poly: op_handle must be a single polynomial in M");
+  }
+  cudaStream_t s = ctx->stream;
+  geom g = make_geom(ctx, 1);
+  void* V;
+  TRY(scratch(ctx, "gmres_V", field_bytes(g, MMC_F64) * (m + 1), &V));
+  std::vector<uint2> ids(g.npad, make_uint2(0u, 0u));
+  void* dids;
+  TRY(scratch(ctx, "ids", ids.size() * sizeof(uint2), &dids));
+  CK(cudaMemcpyAsync(dids, ids.data(), ids.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+  CK(mmc::launch_noise(MMC_F64, g, (const uint2*)dids, MMC_TAG_GMRES, ctx->seed, V, nullptr, s));
+  ArnoldiOut ao;
+  auto op = [&](const void* in, void* out) { return apply_op_f64(ctx, op_handle, in, out, 1, s); };
+  TRY(arnoldi_cgs2(ctx, g, MMC_F64, V, m, op, ao, s));
+  for (int j = 0; j < m; ++j)
+    if (ao.H[0](j + 1, j) == cd(0, 0) && j < m - 1) RET(MMC_ERR_BREAKDOWN, "Arnoldi breakdown");
+  std::vector<cd> th;
+  if (!mmc::harmonic_ritz(ao.H[0], m, th)) RET(MMC_ERR_NOCONV, "harmonic Ritz eigenvalues did not converge");
+  th = mmc::leja_order(th);
+  for (auto& t : th)
+    if (!std::isfinite(t.real()) || !std::isfinite(t.imag()) || t == cd(0, 0)) RET(MMC_ERR_NAN, "bad Ritz value");
+  Poly P;
+  P.kind = 0;
+  P.theta = th;
+  P.op = op_handle;
+  ctx->polys.push_back(P);
+  *handle = int(ctx->polys.size()) - 1;
+  if (theta_out)
+    for (int i = 0; i < m; ++i) {
+      theta_out[2 * i] = th[i].real();
+      theta_out[2 * i + 1] = th[i].imag();
+    }
+  return MMC_OK;
+}
+
+int mmc_harmonic_ritz(int m, const double* H, int ldh, double* theta_out) {
+  if (m < 1 || !H || !theta_out || ldh < m + 1) return MMC_ERR_ARG;
+  CMat Hm(m + 1, m);
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i <= m; ++i) Hm(i, j) = cd(H[2 * (i + size_t(j) * ldh)], H[2 * (i + size_t(j) * ldh) + 1]);
+  std::vector<cd> th;
+  if (!mmc::harmonic_ritz(Hm, m, th)) return MMC_ERR_NOCONV;
+  th = mmc::leja_order(th);
+  for (int i = 0; i < m; ++i) {
+    theta_out[2 * i] = th[i].real();
+    theta_out[2 * i + 1] = th[i].imag();
+  }
+  return MMC_OK;
+}
+
+int mmc_leja_order(int m, const double* in, double* out) {
+  if (m < 0 || (m && (!in || !out))) return MMC_ERR_ARG;
+  std::vector<cd> p(m);
+  for (int i = 0; i < m; ++i) p[i] = cd(in[2 * i], in[2 * i + 1]);
+  p = mmc::leja_order(p);
+  for (int i = 0; i < m; ++i) {
+    out[2 * i] = p[i].real();
+    out[2 * i + 1] = p[i].imag();
+  }
+  return MMC_OK;
+}
+
+int mmc_eig(int n, const double* A, int lda, double* w, double* vr) {
+  if (n < 1 || !A || !w || lda < n) return MMC_ERR_ARG;
+  CMat M(n, n);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) M(i, j) = cd(A[2 * (i + size_t(j) * lda)], A[2 * (i + size_t(j) * lda) + 1]);
+  std::vector<cd> ev;
+  CMat Vr;
+  if (!mmc::eig(M, ev, vr ? &Vr : nullptr)) return MMC_ERR_NOCONV;
+  for (int i = 0; i < n; ++i) {
+    w[2 * i] = ev[i].real();
+    w[2 * i + 1] = ev[i].imag();
+  }
+  if (vr)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        vr[2 * (i + size_t(j) * n)] = Vr(i, j).real();
+        vr[2 * (i + size_t(j) * n) + 1] = Vr(i, j).imag();
+      }
+  return MMC_OK;
+}
+
+}  // extern "C"

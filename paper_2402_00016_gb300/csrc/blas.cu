@@ -1,0 +1,611 @@
+// Field kernels around the stencil: Z(4) noise from Philox4x32-10, probe
+// vectors, layout conversion, and the batched dot products / updates that
+// the CGS2 Arnoldi process, the solves and the deflation projections use.
+// Every reduction is two-stage (per-CTA partial, then a fixed-order sum over
+// CTAs) so results do not depend on scheduling.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mmc {
+namespace {
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): per round, words 0 and 2 are
+// multiplied by two 32-bit constants; the high halves are mixed with words 1
+// and 3 and the round key, the low halves become words 1 and 3; the key gets
+// two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+template <typename T>
+__device__ __forceinline__ void put(T* f, size_t i, double re, double im);
+template <>
+__device__ __forceinline__ void put<double2>(double2* f, size_t i, double re, double im) {
+  f[i] = make_double2(re, im);
+}
+template <>
+__device__ __forceinline__ void put<float2>(float2* f, size_t i, double re, double im) {
+  f[i] = make_float2(float(re), float(im));
+}
+template <>
+__device__ __forceinline__ void put<__nv_bfloat162>(__nv_bfloat162* f, size_t i, double re, double im) {
+  f[i] = __float22bfloat162_rn(make_float2(float(re), float(im)));
+}
+
+template <typename T>
+__device__ __forceinline__ double2 get(const T* f, size_t i);
+template <>
+__device__ __forceinline__ double2 get<double2>(const double2* f, size_t i) {
+  return f[i];
+}
+template <>
+__device__ __forceinline__ double2 get<float2>(const float2* f, size_t i) {
+  float2 v = f[i];
+  return make_double2(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ double2 get<__nv_bfloat162>(const __nv_bfloat162* f, size_t i) {
+  float2 v = __bfloat1622float2(f[i]);
+  return make_double2(v.x, v.y);
+}
+
+__device__ __forceinline__ size_t fidx(const geom& g, int rb, int site, int c, int r) {
+  return ((size_t(rb) * g.V + site) * 12 + c) * g.R + r;
+}
+
+// thread -> (rb = blockIdx.y, site, r) with R lanes per site
+template <typename T>
+__global__ void noise_kernel(geom g, const uint2* ids, uint32_t tag, uint32_t k0, uint32_t k1, T* field,
+                             uint32_t* codes) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  const uint2 id = ids[rb * g.R + r];
+  uint32_t w0 = 0;
+  const bool live = id.x != 0xffffffffu;
+  if (live) w0 = philox10(make_uint4(uint32_t(site), id.y, id.x, tag), k0, k1).x;
+  if (codes) codes[(size_t(rb) * g.V + site) * g.R + r] = w0;
+  if (field) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      uint32_t k = (w0 >> (2 * c)) & 3u;
+      double re = (k == 0) ? 1.0 : (k == 2 ? -1.0 : 0.0);
+      double im = (k == 1) ? 1.0 : (k == 3 ? -1.0 : 0.0);
+      if (!live) re = im = 0.0;
+      put<T>(field, fidx(g, rb, site, c, r), re, im);
+    }
+  }
+}
+
+template <typename T>
+__global__ void probe_kernel(geom g, const int* site_colour, const int2* probe, T* field) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  const int2 pr = probe[rb * g.R + r];  // (colour, component); colour < 0: padding
+  const bool on = pr.x >= 0 && site_colour[site] == pr.x;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) put<T>(field, fidx(g, rb, site, c, r), (on && c == pr.y) ? 1.0 : 0.0, 0.0);
+}
+
+template <typename T>
+__global__ void pack_kernel(geom g, int nrhs, const double2* canon, T* field) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  const int rg = rb * g.R + r;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    double2 v = (rg < nrhs) ? canon[(size_t(rg) * g.V + site) * 12 + c] : make_double2(0.0, 0.0);
+    put<T>(field, fidx(g, rb, site, c, r), v.x, v.y);
+  }
+}
+
+template <typename T>
+__global__ void unpack_kernel(geom g, int nrhs, const T* field, double2* canon) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  const int rg = rb * g.R + r;
+  if (rg >= nrhs) return;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) canon[(size_t(rg) * g.V + site) * 12 + c] = get<T>(field, fidx(g, rb, site, c, r));
+}
+
+template <typename D, typename S>
+__global__ void convert_kernel(size_t n, D* dst, const S* src) {
+  size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  size_t stride = size_t(gridDim.x) * blockDim.x;
+  for (; i < n; i += stride) {
+    double2 v = get<S>(src, i);
+    put<D>(dst, i, v.x, v.y);
+  }
+}
+
+// Reduce (re, im) over the threads of the CTA that share r = threadIdx.x % R;
+// thread r < R of the CTA returns the total in (re, im).
+__device__ __forceinline__ void cta_reduce_r(double& re, double& im, int R, double2* sh) {
+  for (int off = R; off < 32; off <<= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
+  }
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  __syncthreads();
+  if (wl < R && wl < 32) sh[warp * 32 + wl] = make_double2(re, im);
+  __syncthreads();
+  if (threadIdx.x < R) {
+    double sr = 0, si = 0;
+    for (int w = 0; w < nw; ++w) {
+      sr += sh[w * 32 + threadIdx.x].x;
+      si += sh[w * 32 + threadIdx.x].y;
+    }
+    re = sr;
+    im = si;
+  }
+}
+
+// conj(a) * (Theta w) accumulated over 12 components
+__device__ __forceinline__ void theta_dot(const double2 (&a)[12], const double2 (&w)[12], int theta, double& re,
+                                          double& im) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    int src = (theta == 1) ? (c + 6) % 12 : c;
+    double sg = (theta == 2 && c >= 6) ? -1.0 : 1.0;
+    double2 x = w[src];
+    re += sg * (a[c].x * x.x + a[c].y * x.y);
+    im += sg * (a[c].x * x.y - a[c].y * x.x);
+  }
+}
+
+template <typename T>
+__global__ void multidot_kernel(geom g, const T* A, size_t a_stride, int nvec, const T* w, int theta, int spc,
+                                double2* partial) {
+  __shared__ double2 sh[8 * 32];
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int spp = blockDim.x / g.R;
+  const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
+  for (int i = 0; i < nvec; ++i) {
+    double re = 0, im = 0;
+    for (int s0 = s_begin; s0 < s_end; s0 += spp) {
+      int site = s0 + threadIdx.x / g.R;
+      if (site >= s_end) continue;
+      double2 a[12], x[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        a[c] = get<T>(A + size_t(i) * a_stride, fidx(g, rb, site, c, r));
+        x[c] = get<T>(w, fidx(g, rb, site, c, r));
+      }
+      theta_dot(a, x, theta, re, im);
+    }
+    cta_reduce_r(re, im, g.R, sh);
+    if (threadIdx.x < g.R)
+      partial[(size_t(blockIdx.x) * nvec + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(re, im);
+  }
+}
+
+__global__ void reduce_kernel(const double2* partial, int nbx, int nvec, int npad, double2* out, int accumulate) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nvec * npad) return;
+  double re = 0, im = 0;
+  for (int b = 0; b < nbx; ++b) {
+    double2 v = partial[size_t(b) * nvec * npad + idx];
+    re += v.x;
+    im += v.y;
+  }
+  if (accumulate) {
+    re += out[idx].x;
+    im += out[idx].y;
+  }
+  out[idx] = make_double2(re, im);
+}
+
+template <typename T>
+__global__ void basis_update_kernel(geom g, const T* A, size_t a_stride, int nvec, const double2* h, T* w) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  const int rg = rb * g.R + r;
+#pragma unroll 1
+  for (int c = 0; c < 12; ++c) {
+    size_t e = fidx(g, rb, site, c, r);
+    double2 acc = get<T>(w, e);
+    for (int i = 0; i < nvec; ++i) {
+      double2 a = get<T>(A + size_t(i) * a_stride, e);
+      double2 hh = h[size_t(i) * g.npad + rg];
+      acc.x -= a.x * hh.x - a.y * hh.y;
+      acc.y -= a.x * hh.y + a.y * hh.x;
+    }
+    put<T>(w, e, acc.x, acc.y);
+  }
+}
+
+template <typename T>
+__global__ void normalise_kernel(geom g, const T* src, const double2* nrm2, T* dst) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  double n2 = nrm2[rb * g.R + r].x;
+  double sc = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    size_t e = fidx(g, rb, site, c, r);
+    double2 v = get<T>(src, e);
+    put<T>(dst, e, v.x * sc, v.y * sc);
+  }
+}
+
+template <typename T>
+__global__ void axpby_kernel(geom g, const double2* a, const T* x, const double2* b, T* y) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  const int rg = rb * g.R + r;
+  double2 ca = a ? a[rg] : make_double2(0, 0), cb = b ? b[rg] : make_double2(0, 0);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    size_t e = fidx(g, rb, site, c, r);
+    double2 xv = x ? get<T>(x, e) : make_double2(0, 0);
+    double2 yv = b ? get<T>(y, e) : make_double2(0, 0);
+    double re = ca.x * xv.x - ca.y * xv.y + cb.x * yv.x - cb.y * yv.y;
+    double im = ca.x * xv.y + ca.y * xv.x + cb.x * yv.y + cb.y * yv.x;
+    put<T>(y, e, re, im);
+  }
+}
+
+template <typename T>
+__global__ void gamma_kernel(geom g, int theta, const T* src, T* dst) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  double2 v[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) v[c] = get<T>(src, fidx(g, rb, site, c, r));
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    int s = (theta == 1) ? (c + 6) % 12 : c;
+    double sg = (theta == 2 && c >= 6) ? -1.0 : 1.0;
+    put<T>(dst, fidx(g, rb, site, c, r), sg * v[s].x, sg * v[s].y);
+  }
+}
+
+template <typename T>
+__global__ void bilinear_codes_kernel(geom g, const uint32_t* codes, int theta, const T* x, int spc,
+                                      double2* partial) {
+  __shared__ double2 sh[8 * 32];
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int spp = blockDim.x / g.R;
+  const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
+  double re = 0, im = 0;
+  for (int s0 = s_begin; s0 < s_end; s0 += spp) {
+    int site = s0 + threadIdx.x / g.R;
+    if (site >= s_end) continue;
+    uint32_t code = codes[(size_t(rb) * g.V + site) * g.R + r];
+    double2 a[12], xv[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      uint32_t k = (code >> (2 * c)) & 3u;
+      a[c] = make_double2(k == 0 ? 1.0 : (k == 2 ? -1.0 : 0.0), k == 1 ? 1.0 : (k == 3 ? -1.0 : 0.0));
+      xv[c] = get<T>(x, fidx(g, rb, site, c, r));
+    }
+    theta_dot(a, xv, theta, re, im);
+  }
+  cta_reduce_r(re, im, g.R, sh);
+  if (threadIdx.x < g.R) {
+    double2* d = partial + size_t(blockIdx.x) * g.npad + rb * g.R + threadIdx.x;
+    double2 cur = *d;
+    *d = make_double2(cur.x + re, cur.y + im);
+  }
+}
+
+// a[i][r] = sum conj(eta_r) Theta z_i ; b[i][r] = sum conj(u_i) eta_r.  z_i, u_i are
+// single-vector FP64 fields ([site][12], R = 1 layout).
+__global__ void defl_proj_kernel(geom g, const uint32_t* codes, int theta, const double2* Z, const double2* U,
+                                 int k, int spc, double2* pa, double2* pb) {
+  __shared__ double2 sh[8 * 32];
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int spp = blockDim.x / g.R;
+  const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
+  const size_t n = size_t(g.V) * 12;
+  for (int i = 0; i < k; ++i) {
+    double are = 0, aim = 0, bre = 0, bim = 0;
+    for (int s0 = s_begin; s0 < s_end; s0 += spp) {
+      int site = s0 + threadIdx.x / g.R;
+      if (site >= s_end) continue;
+      uint32_t code = codes[(size_t(rb) * g.V + site) * g.R + r];
+      double2 eta[12], z[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        uint32_t kk = (code >> (2 * c)) & 3u;
+        eta[c] = make_double2(kk == 0 ? 1.0 : (kk == 2 ? -1.0 : 0.0), kk == 1 ? 1.0 : (kk == 3 ? -1.0 : 0.0));
+        z[c] = Z[size_t(i) * n + size_t(site) * 12 + c];
+      }
+      theta_dot(eta, z, theta, are, aim);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        double2 u = U[size_t(i) * n + size_t(site) * 12 + c];
+        bre += u.x * eta[c].x + u.y * eta[c].y;
+        bim += u.x * eta[c].y - u.y * eta[c].x;
+      }
+    }
+    cta_reduce_r(are, aim, g.R, sh);
+    if (threadIdx.x < g.R) pa[(size_t(blockIdx.x) * k + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(are, aim);
+    cta_reduce_r(bre, bim, g.R, sh);
+    if (threadIdx.x < g.R) pb[(size_t(blockIdx.x) * k + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(bre, bim);
+  }
+}
+
+// c[i][r] (partial) = sum over the CTA's sites of conj(v_i) . f_r, v_i single-vector FP64 fields.
+template <typename T>
+__global__ void vec_proj_kernel(geom g, const double2* Vv, int k, const T* f, int spc, double2* partial) {
+  __shared__ double2 sh[8 * 32];
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int spp = blockDim.x / g.R;
+  const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
+  const size_t n = size_t(g.V) * 12;
+  for (int i = 0; i < k; ++i) {
+    double re = 0, im = 0;
+    for (int s0 = s_begin; s0 < s_end; s0 += spp) {
+      int site = s0 + threadIdx.x / g.R;
+      if (site >= s_end) continue;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        double2 v = Vv[size_t(i) * n + size_t(site) * 12 + c];
+        double2 x = get<T>(f, fidx(g, rb, site, c, r));
+        re += v.x * x.x + v.y * x.y;
+        im += v.x * x.y - v.y * x.x;
+      }
+    }
+    cta_reduce_r(re, im, g.R, sh);
+    if (threadIdx.x < g.R) partial[(size_t(blockIdx.x) * k + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(re, im);
+  }
+}
+
+// f_r += sum_i v_i coef[i][r], v_i single-vector FP64 fields.
+template <typename T>
+__global__ void vec_update_kernel(geom g, const double2* Vv, int k, const double2* coef, T* f) {
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  const int rg = rb * g.R + r;
+  const size_t n = size_t(g.V) * 12;
+#pragma unroll 1
+  for (int c = 0; c < 12; ++c) {
+    size_t e = fidx(g, rb, site, c, r);
+    double2 acc = get<T>(f, e);
+    for (int i = 0; i < k; ++i) {
+      double2 v = Vv[size_t(i) * n + size_t(site) * 12 + c];
+      double2 h = coef[size_t(i) * g.npad + rg];
+      acc.x += v.x * h.x - v.y * h.y;
+      acc.y += v.x * h.y + v.y * h.x;
+    }
+    put<T>(f, e, acc.x, acc.y);
+  }
+}
+
+__global__ void add2_kernel(const double2* a, const double2* b, double2* out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2(a[i].x + b[i].x, a[i].y + b[i].y);
+}
+
+inline dim3 site_grid(const geom& g, int threads) {
+  size_t total = size_t(g.V) * g.R;
+  return dim3(unsigned((total + threads - 1) / threads), unsigned(g.nrb));
+}
+
+}  // namespace
+
+#define MMC_DISPATCH3(prec, F, ...)                          \
+  do {                                                      \
+    if ((prec) == 0) F<double2> __VA_ARGS__;                \
+    else if ((prec) == 1) F<float2> __VA_ARGS__;            \
+    else F<__nv_bfloat162> __VA_ARGS__;                     \
+  } while (0)
+
+cudaError_t launch_noise(int prec, geom g, const uint2* ids, uint32_t tag, uint64_t seed, void* field,
+                         uint32_t* codes, cudaStream_t s) {
+  const int th = 256;
+  dim3 grid = site_grid(g, th);
+  uint32_t k0 = uint32_t(seed & 0xffffffffu), k1 = uint32_t(seed >> 32);
+  if (prec == 0)
+    noise_kernel<double2><<<grid, th, 0, s>>>(g, ids, tag, k0, k1, (double2*)field, codes);
+  else if (prec == 1)
+    noise_kernel<float2><<<grid, th, 0, s>>>(g, ids, tag, k0, k1, (float2*)field, codes);
+  else
+    noise_kernel<__nv_bfloat162><<<grid, th, 0, s>>>(g, ids, tag, k0, k1, (__nv_bfloat162*)field, codes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe(int prec, geom g, const int* site_colour, const int2* probe, void* field,
+                         cudaStream_t s) {
+  const int th = 256;
+  dim3 grid = site_grid(g, th);
+  if (prec == 0)
+    probe_kernel<double2><<<grid, th, 0, s>>>(g, site_colour, probe, (double2*)field);
+  else if (prec == 1)
+    probe_kernel<float2><<<grid, th, 0, s>>>(g, site_colour, probe, (float2*)field);
+  else
+    probe_kernel<__nv_bfloat162><<<grid, th, 0, s>>>(g, site_colour, probe, (__nv_bfloat162*)field);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int prec, geom g, int nrhs, const double2* canon, void* field, cudaStream_t s) {
+  const int th = 256;
+  dim3 grid = site_grid(g, th);
+  if (prec == 0)
+    pack_kernel<double2><<<grid, th, 0, s>>>(g, nrhs, canon, (double2*)field);
+  else if (prec == 1)
+    pack_kernel<float2><<<grid, th, 0, s>>>(g, nrhs, canon, (float2*)field);
+  else
+    pack_kernel<__nv_bfloat162><<<grid, th, 0, s>>>(g, nrhs, canon, (__nv_bfloat162*)field);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int prec, geom g, int nrhs, const void* field, double2* canon, cudaStream_t s) {
+  const int th = 256;
+  dim3 grid = site_grid(g, th);
+  if (prec == 0)
+    unpack_kernel<double2><<<grid, th, 0, s>>>(g, nrhs, (const double2*)field, canon);
+  else if (prec == 1)
+    unpack_kernel<float2><<<grid, th, 0, s>>>(g, nrhs, (const float2*)field, canon);
+  else
+    unpack_kernel<__nv_bfloat162><<<grid, th, 0, s>>>(g, nrhs, (const __nv_bfloat162*)field, canon);
+  return cudaGetLastError();
+}
+
+template <typename D>
+static void convert_from(int ps, size_t n, D* dst, const void* src, cudaStream_t s) {
+  unsigned blocks = unsigned(std::min<size_t>((n + 255) / 256, 152 * 64));
+  if (ps == 0)
+    convert_kernel<D, double2><<<blocks, 256, 0, s>>>(n, dst, (const double2*)src);
+  else if (ps == 1)
+    convert_kernel<D, float2><<<blocks, 256, 0, s>>>(n, dst, (const float2*)src);
+  else
+    convert_kernel<D, __nv_bfloat162><<<blocks, 256, 0, s>>>(n, dst, (const __nv_bfloat162*)src);
+}
+
+cudaError_t launch_convert(int pd, void* dst, int ps, const void* src, geom g, cudaStream_t s) {
+  size_t n = size_t(g.nrb) * g.V * 12 * g.R;
+  if (pd == 0)
+    convert_from<double2>(ps, n, (double2*)dst, src, s);
+  else if (pd == 1)
+    convert_from<float2>(ps, n, (float2*)dst, src, s);
+  else
+    convert_from<__nv_bfloat162>(ps, n, (__nv_bfloat162*)dst, src, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multidot(int prec, geom g, const void* A, size_t a_stride, int nvec, const void* w, int theta,
+                            int spc, double2* partial, cudaStream_t s) {
+  dim3 grid((g.V + spc - 1) / spc, g.nrb);
+  if (prec == 0)
+    multidot_kernel<double2><<<grid, 256, 0, s>>>(g, (const double2*)A, a_stride, nvec, (const double2*)w, theta,
+                                                  spc, partial);
+  else
+    multidot_kernel<float2><<<grid, 256, 0, s>>>(g, (const float2*)A, a_stride, nvec, (const float2*)w, theta, spc,
+                                                 partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double2* partial, int nbx, int nvec, int npad, double2* out, int accumulate,
+                          cudaStream_t s) {
+  int n = nvec * npad;
+  reduce_kernel<<<(n + 127) / 128, 128, 0, s>>>(partial, nbx, nvec, npad, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_basis_update(int prec, geom g, const void* A, size_t a_stride, int nvec, const double2* h,
+                                void* w, cudaStream_t s) {
+  dim3 grid = site_grid(g, 256);
+  if (prec == 0)
+    basis_update_kernel<double2><<<grid, 256, 0, s>>>(g, (const double2*)A, a_stride, nvec, h, (double2*)w);
+  else
+    basis_update_kernel<float2><<<grid, 256, 0, s>>>(g, (const float2*)A, a_stride, nvec, h, (float2*)w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalise(int prec, geom g, const void* src, const double2* nrm2, void* dst, cudaStream_t s) {
+  dim3 grid = site_grid(g, 256);
+  if (prec == 0)
+    normalise_kernel<double2><<<grid, 256, 0, s>>>(g, (const double2*)src, nrm2, (double2*)dst);
+  else
+    normalise_kernel<float2><<<grid, 256, 0, s>>>(g, (const float2*)src, nrm2, (float2*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(int prec, geom g, const double2* a, const void* x, const double2* b, void* y,
+                         cudaStream_t s) {
+  dim3 grid = site_grid(g, 256);
+  if (prec == 0)
+    axpby_kernel<double2><<<grid, 256, 0, s>>>(g, a, (const double2*)x, b, (double2*)y);
+  else if (prec == 1)
+    axpby_kernel<float2><<<grid, 256, 0, s>>>(g, a, (const float2*)x, b, (float2*)y);
+  else
+    axpby_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>(g, a, (const __nv_bfloat162*)x, b, (__nv_bfloat162*)y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gamma(int prec, geom g, int theta, const void* src, void* dst, cudaStream_t s) {
+  dim3 grid = site_grid(g, 256);
+  if (prec == 0)
+    gamma_kernel<double2><<<grid, 256, 0, s>>>(g, theta, (const double2*)src, (double2*)dst);
+  else if (prec == 1)
+    gamma_kernel<float2><<<grid, 256, 0, s>>>(g, theta, (const float2*)src, (float2*)dst);
+  else
+    gamma_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>(g, theta, (const __nv_bfloat162*)src, (__nv_bfloat162*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bilinear_codes(int prec, geom g, const uint32_t* codes, int theta, const void* x, int spc,
+                                  double2* partial, cudaStream_t s) {
+  dim3 grid((g.V + spc - 1) / spc, g.nrb);
+  if (prec == 0)
+    bilinear_codes_kernel<double2><<<grid, 256, 0, s>>>(g, codes, theta, (const double2*)x, spc, partial);
+  else if (prec == 1)
+    bilinear_codes_kernel<float2><<<grid, 256, 0, s>>>(g, codes, theta, (const float2*)x, spc, partial);
+  else
+    bilinear_codes_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>(g, codes, theta, (const __nv_bfloat162*)x, spc,
+                                                               partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defl_proj(geom g, const uint32_t* codes, int theta, const double2* Z, const double2* U, int k,
+                             int spc, double2* pa, double2* pb, cudaStream_t s) {
+  dim3 grid((g.V + spc - 1) / spc, g.nrb);
+  defl_proj_kernel<<<grid, 256, 0, s>>>(g, codes, theta, Z, U, k, spc, pa, pb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_proj(int prec, geom g, const double2* Vv, int k, const void* f, int spc, double2* partial,
+                            cudaStream_t s) {
+  dim3 grid((g.V + spc - 1) / spc, g.nrb);
+  if (prec == 0)
+    vec_proj_kernel<double2><<<grid, 256, 0, s>>>(g, Vv, k, (const double2*)f, spc, partial);
+  else
+    vec_proj_kernel<float2><<<grid, 256, 0, s>>>(g, Vv, k, (const float2*)f, spc, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_update(int prec, geom g, const double2* Vv, int k, const double2* coef, void* f,
+                              cudaStream_t s) {
+  dim3 grid = site_grid(g, 256);
+  if (prec == 0)
+    vec_update_kernel<double2><<<grid, 256, 0, s>>>(g, Vv, k, coef, (double2*)f);
+  else
+    vec_update_kernel<float2><<<grid, 256, 0, s>>>(g, Vv, k, coef, (float2*)f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add2(const double2* a, const double2* b, double2* out, int n, cudaStream_t s) {
+  add2_kernel<<<(n + 127) / 128, 128, 0, s>>>(a, b, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mmc

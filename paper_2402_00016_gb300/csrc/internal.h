@@ -1,0 +1,481 @@
+// Internals shared by the host translation units: the context, scratch
+// buffers, the step-program runner, polynomial programs and the Arnoldi
+// process.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mmc.h"
+#include "dense.h"
+#include "kernels.h"
+
+namespace mmc {
+namespace host {
+
+struct Poly {
+  int kind = 0;                 // 0: single in `base`, 1: double
+  std::vector<cd> theta;        // single: Leja-ordered roots
+  int op = MMC_OP_M;            // single: MMC_OP_M, or handle h (a polynomial in phi_h)
+  int h_in = -1, h_out = -1;    // double: p_in in M, p_out in phi_in
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace host
+}  // namespace mmc
+
+struct mmc_ctx {
+  int dims[4] = {0, 0, 0, 0};
+  int V = 0;
+  uint64_t seed = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double kappa = 0;
+  int tap = 1;
+  bool gauge = false;
+  void* links64 = nullptr;
+  void* links32 = nullptr;
+  std::vector<mmc::host::Poly> polys;
+  // deflation data (FP64 single-vector fields [site][12])
+  int k_defl = 0;
+  std::vector<mmc::cd> lambda;
+  double2* Z = nullptr;
+  double2* U = nullptr;
+  std::map<std::string, mmc::host::DevBuf> scratch;
+  std::string err;
+  long long matvecs = 0;
+  int spc_step = 64;  // sites per CTA of the step kernel
+};
+
+namespace mmc {
+namespace host {
+using mmc::cd;
+using mmc::CMat;
+using mmc::geom;
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+      return MMC_ERR_CUDA;                                                              \
+    }                                                                                   \
+  } while (0)
+
+#define RET(code, msg)    \
+  do {                    \
+    ctx->err = (msg);     \
+    return (code);        \
+  } while (0)
+
+#define TRY(expr)          \
+  do {                     \
+    int rc_ = (expr);      \
+    if (rc_ != MMC_OK) return rc_; \
+  } while (0)
+
+inline size_t elem_bytes(int prec) { return prec == MMC_F64 ? 16 : (prec == MMC_F32 ? 8 : 4); }
+
+inline int rhs_block(int nrhs) {
+  int R = 1;
+  while (R < nrhs && R < 16) R <<= 1;
+  return R;
+}
+
+inline geom make_geom(const mmc_ctx* ctx, int nrhs) {
+  geom g;
+  g.V = ctx->V;
+  g.R = rhs_block(nrhs);
+  g.nrb = (nrhs + g.R - 1) / g.R;
+  g.npad = g.nrb * g.R;
+  return g;
+}
+
+inline size_t field_bytes(const geom& g, int prec) { return size_t(g.npad) * g.V * 12 * elem_bytes(prec); }
+
+// Get (and grow) a named scratch buffer owned by the context.
+inline int scratch(mmc_ctx* ctx, const std::string& key, size_t bytes, void** out) {
+  DevBuf& b = ctx->scratch[key];
+  if (b.bytes < bytes) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      b.p = nullptr;
+      ctx->err = "cudaMalloc(" + key + ", " + std::to_string(bytes) + "): " + cudaGetErrorString(e);
+      return MMC_ERR_NOMEM;
+    }
+    b.bytes = bytes;
+  }
+  *out = b.p;
+  return MMC_OK;
+}
+
+inline int rpt_for(int prec, int R) {
+  if (prec == MMC_F64) return 1;
+  if (prec == MMC_F32) return R >= 2 ? 2 : 1;
+  return R >= 2 ? 2 : 1;
+}
+
+inline int log2i(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// ------------------------------------------------------------- step runner
+struct Step {
+  const void* in = nullptr;
+  void* out = nullptr;
+  const void* aux = nullptr;
+  int flags = 0;
+  std::vector<cd> coef;  // [5][npad]
+};
+
+struct Run {
+  geom g;
+  int prec = MMC_F64;
+  void* y = nullptr;              // accumulator field (double2 for F64, float2 otherwise)
+  const uint32_t* codes = nullptr;
+  const void* left = nullptr;
+  int theta = 0;
+  double2* partial = nullptr;     // [nbx][npad]
+  int nbx = 0;
+  const int* rb_len = nullptr;
+  bool dagger = false;
+  std::vector<Step> steps;
+};
+
+inline int nbx_for(const mmc_ctx* ctx, int spc) { return (ctx->V + spc - 1) / spc; }
+
+inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
+  if (run.steps.empty()) return MMC_OK;
+  const geom& g = run.g;
+  const size_t per = size_t(5) * g.npad;
+  std::vector<double2> host(per * run.steps.size());
+  for (size_t k = 0; k < run.steps.size(); ++k)
+    for (size_t i = 0; i < per; ++i)
+      host[k * per + i] = make_double2(run.steps[k].coef[i].real(), run.steps[k].coef[i].imag());
+  void* dcoef;
+  TRY(scratch(ctx, "coef", host.size() * sizeof(double2), &dcoef));
+  CK(cudaMemcpyAsync(dcoef, host.data(), host.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  const int rpt = rpt_for(run.prec, g.R);
+  for (size_t k = 0; k < run.steps.size(); ++k) {
+    const Step& st = run.steps[k];
+    mmc::step_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.in = st.in;
+    p.out = st.out;
+    p.aux = st.aux;
+    p.y = run.y;
+    p.codes = run.codes;
+    p.left = run.left;
+    p.coef = reinterpret_cast<const double2*>(dcoef) + k * per;
+    p.partial = run.partial;
+    p.links = run.prec == MMC_F64 ? ctx->links64 : ctx->links32;
+    p.rb_len = run.rb_len;
+    p.step = int(k);
+    p.V = ctx->V;
+    p.R = g.R;
+    p.logL = log2i(g.R / rpt);
+    p.npad = g.npad;
+    p.spc = ctx->spc_step;
+    p.Lx = ctx->dims[0];
+    p.Ly = ctx->dims[1];
+    p.Lz = ctx->dims[2];
+    p.Lt = ctx->dims[3];
+    p.tap = ctx->tap;
+    p.theta = run.theta;
+    p.flags = st.flags | (run.dagger ? mmc::SF_DAGGER : 0);
+    CK(mmc::launch_step(run.prec, rpt, p, g.nrb, s));
+    if (st.flags & mmc::SF_HOP) ctx->matvecs += g.npad;
+  }
+  return MMC_OK;
+}
+
+inline std::vector<cd> coef_block(int npad) { return std::vector<cd>(size_t(5) * npad, cd(0, 0)); }
+
+// coefficient setter for rhs r: out = a in + b D in + g aux; accumulations w_in, w_out
+inline void set_coef(std::vector<cd>& c, int npad, int r, cd a, cd b, cd gg, cd wi, cd wo) {
+  c[0 * size_t(npad) + r] = a;
+  c[1 * size_t(npad) + r] = b;
+  c[2 * size_t(npad) + r] = gg;
+  c[3 * size_t(npad) + r] = wi;
+  c[4 * size_t(npad) + r] = wo;
+}
+
+// Accumulation mode of a polynomial program.
+enum AccMode { ACC_Y = 0, ACC_BIL = 1 };
+
+inline int acc_flags(AccMode m, const Run& run) {
+  if (m == ACC_Y) return mmc::SF_YACC;
+  return run.codes ? mmc::SF_BIL_CODES : mmc::SF_BIL_LEFT;
+}
+
+// Append the steps of a single polynomial p (roots th, in M) applied to the field `x`:
+// accumulates sum_k u_k (Sec. 3) into y (ACC_Y) or into the bilinear (ACC_BIL).
+// Ping-pong buffers P0, P1.  `scale` multiplies every accumulated term.
+inline void build_single(const mmc_ctx* ctx, Run& run, const std::vector<cd>& th, const void* x, void* P0, void* P1,
+                  AccMode mode, cd scale, int nrhs) {
+  const int m = int(th.size());
+  const int npad = run.g.npad;
+  const double kap = ctx->kappa;
+  const int accf = acc_flags(mode, run);
+  if (m == 1) {
+    Step st;
+    st.in = x;
+    st.flags = accf;
+    st.coef = coef_block(npad);
+    for (int r = 0; r < nrhs; ++r) set_coef(st.coef, npad, r, 0, 0, 0, scale / th[0], 0);
+    run.steps.push_back(st);
+    return;
+  }
+  void* P[2] = {P0, P1};
+  for (int k = 0; k < m - 1; ++k) {
+    Step st;
+    st.in = (k == 0) ? x : P[(k - 1) & 1];
+    st.out = P[k & 1];
+    st.flags = mmc::SF_HOP | mmc::SF_WRITE | accf;
+    if (k == m - 2) st.flags |= mmc::SF_BIL_OUT;  // the last prod's term rides on this step
+    st.coef = coef_block(npad);
+    cd it = 1.0 / th[k];
+    cd wo = (k == m - 2) ? scale / th[m - 1] : cd(0, 0);
+    for (int r = 0; r < nrhs; ++r) set_coef(st.coef, npad, r, 1.0 - it, kap * it, 0, scale * it, wo);
+    run.steps.push_back(st);
+  }
+}
+
+// Steps of the double polynomial p_in(M) p_out(phi_in(M)) (Sec. 5) applied to the
+// field `w` that already holds p_in(M) x in storage precision (A[0]).  Buffers:
+// P0, P1 (inner ping-pong), A0, A1 (outer iterate).  Accumulates sum_k over
+// p_out's terms into y or the bilinear.
+inline void build_double_outer(const mmc_ctx* ctx, Run& run, const std::vector<cd>& tin, const std::vector<cd>& tout,
+                        void* P0, void* P1, void* A0, void* A1, AccMode mode, int nrhs) {
+  const int mi = int(tin.size()), mo = int(tout.size());
+  const int npad = run.g.npad;
+  const double kap = ctx->kappa;
+  const int accf = acc_flags(mode, run);
+  void* P[2] = {P0, P1};
+  void* A[2] = {A0, A1};
+  if (mo == 1) {
+    Step st;
+    st.in = A[0];
+    st.flags = accf;
+    st.coef = coef_block(npad);
+    for (int r = 0; r < nrhs; ++r) set_coef(st.coef, npad, r, 0, 0, 0, 1.0 / tout[0], 0);
+    run.steps.push_back(st);
+    return;
+  }
+  for (int k = 0; k < mo - 1; ++k) {
+    const cd io = 1.0 / tout[k];
+    for (int j = 0; j < mi; ++j) {
+      Step st;
+      st.coef = coef_block(npad);
+      const cd ii = 1.0 / tin[j];
+      const bool first = (j == 0), last = (j == mi - 1);
+      st.in = first ? A[k & 1] : P[(j - 1) & 1];
+      st.out = last ? A[(k + 1) & 1] : P[j & 1];
+      st.flags = mmc::SF_HOP | mmc::SF_WRITE;
+      cd a = 1.0 - ii, b = kap * ii, gg = 0, wi = 0, wo = 0;
+      if (first) {
+        st.flags |= accf;
+        wi = io;
+      }
+      if (last) {
+        // prod_{k+1} = (1/theta_out) (pi_in step of q) + (1 - 1/theta_out) prod_k
+        a *= io;
+        b *= io;
+        gg = 1.0 - io;
+        st.aux = A[k & 1];
+        st.flags |= mmc::SF_AUX;
+        if (k == mo - 2) {
+          st.flags |= accf | mmc::SF_BIL_OUT;
+          wo = 1.0 / tout[mo - 1];
+        }
+      }
+      for (int r = 0; r < nrhs; ++r) set_coef(st.coef, npad, r, a, b, gg, wi, wo);
+      run.steps.push_back(st);
+    }
+  }
+}
+
+inline bool valid_poly(const mmc_ctx* ctx, int h) { return h >= 0 && h < int(ctx->polys.size()); }
+
+inline int poly_degree(const mmc_ctx* ctx, int h) {
+  const Poly& P = ctx->polys[h];
+  if (P.kind == 1) {
+    int mi = int(ctx->polys[P.h_in].theta.size()), mo = int(ctx->polys[P.h_out].theta.size());
+    return mi * mo - 1;
+  }
+  int m = int(P.theta.size());
+  if (P.op == MMC_OP_M) return m - 1;
+  int mb = int(ctx->polys[P.op].theta.size());
+  return (m - 1) * mb;  // degree in M of p_out(phi_h), phi_h of degree mb
+}
+
+inline cd poly_value(const mmc_ctx* ctx, int h, cd a) {
+  const Poly& P = ctx->polys[h];
+  if (P.kind == 1) {
+    cd pin = mmc::poly_scalar(ctx->polys[P.h_in].theta, a);
+    return pin * mmc::poly_scalar(ctx->polys[P.h_out].theta, a * pin);
+  }
+  if (P.op == MMC_OP_M) return mmc::poly_scalar(P.theta, a);
+  cd phi = a * mmc::poly_scalar(ctx->polys[P.op].theta, a);
+  return mmc::poly_scalar(P.theta, phi);
+}
+
+// Apply polynomial h to the field x (nrhs vectors, precision prec) with accumulation
+// into y (ACC_Y; y zeroed here, type double2 for F64 / float2 otherwise) or into
+// run.partial (ACC_BIL; with run.codes / run.left set by the caller).
+inline int apply_poly_impl(mmc_ctx* ctx, int h, const void* x, int nrhs, int prec, AccMode mode, void* y,
+                    Run& base, cudaStream_t s) {
+  const Poly& P = ctx->polys[h];
+  geom g = base.g;
+  const size_t fb = field_bytes(g, prec);
+  void *P0, *P1;
+  TRY(scratch(ctx, "P0", fb, &P0));
+  TRY(scratch(ctx, "P1", fb, &P1));
+  const size_t yb = size_t(g.npad) * g.V * 12 * (prec == MMC_F64 ? 16 : 8);
+  if (mode == ACC_Y) CK(cudaMemsetAsync(y, 0, yb, s));
+  if (P.kind == 0 && P.op == MMC_OP_M) {
+    Run run = base;
+    run.y = y;
+    build_single(ctx, run, P.theta, x, P0, P1, mode, 1.0, nrhs);
+    return exec_run(ctx, run, s);
+  }
+  if (P.kind == 0) RET(MMC_ERR_ARG, "polynomial in phi_h is not applicable alone; compose it with mmc_poly_double");
+  const std::vector<cd>& tin = ctx->polys[P.h_in].theta;
+  const std::vector<cd>& tout = ctx->polys[P.h_out].theta;
+  // stage A: w = p_in(M) x as a vector (accumulator), then to storage precision in A0
+  void *A0, *A1, *W;
+  TRY(scratch(ctx, "A0", fb, &A0));
+  TRY(scratch(ctx, "A1", fb, &A1));
+  TRY(scratch(ctx, "W", yb, &W));
+  CK(cudaMemsetAsync(W, 0, yb, s));
+  {
+    Run run = base;
+    run.y = W;
+    run.codes = nullptr;
+    run.left = nullptr;
+    build_single(ctx, run, tin, x, P0, P1, ACC_Y, 1.0, nrhs);
+    TRY(exec_run(ctx, run, s));
+  }
+  CK(mmc::launch_convert(prec, A0, prec == MMC_F64 ? MMC_F64 : MMC_F32, W, g, s));
+  Run run = base;
+  run.y = y;
+  build_double_outer(ctx, run, tin, tout, P0, P1, A0, A1, mode, nrhs);
+  return exec_run(ctx, run, s);
+}
+
+// y = M x (or M^+ x) on a field: a = 1, b = -kappa.
+inline int apply_M_impl(mmc_ctx* ctx, const void* x, void* y, int nrhs, int prec, bool dagger, cudaStream_t s) {
+  Run run;
+  run.g = make_geom(ctx, nrhs);
+  run.prec = prec;
+  run.dagger = dagger;
+  Step st;
+  st.in = x;
+  st.out = y;
+  st.flags = mmc::SF_HOP | mmc::SF_WRITE;
+  st.coef = coef_block(run.g.npad);
+  for (int r = 0; r < run.g.npad; ++r) set_coef(st.coef, run.g.npad, r, 1.0, -ctx->kappa, 0, 0, 0);
+  run.steps.push_back(st);
+  return exec_run(ctx, run, s);
+}
+
+// ----------------------------------------------------------- Arnoldi (CGS2)
+// op(in, out): out = operator applied to in (single-vector or batched FP64 fields)
+// Basis V: (m+1) FP64 fields of geometry g (contiguous), start vector in V[0]
+// (unnormalised on entry).  Fills Hcol (host, per rhs (m+1) x m column-major).
+struct ArnoldiOut {
+  std::vector<CMat> H;  // per rhs
+  std::vector<double> beta;
+};
+
+template <class Op>
+inline int arnoldi_cgs2(mmc_ctx* ctx, const geom& g, int prec, void* V, int m, Op op, ArnoldiOut& out, cudaStream_t s) {
+  const size_t stride = size_t(g.npad) * g.V * 12;  // elements per basis field
+  const size_t eb = elem_bytes(prec);
+  const int spc = 256;
+  const int nbx = (g.V + spc - 1) / spc;
+  void *part, *h1, *h2, *hcols, *nrm, *W;
+  TRY(scratch(ctx, "arn_part", size_t(nbx) * (m + 1) * g.npad * sizeof(double2), &part));
+  TRY(scratch(ctx, "arn_h1", size_t(m + 1) * g.npad * sizeof(double2), &h1));
+  TRY(scratch(ctx, "arn_h2", size_t(m + 1) * g.npad * sizeof(double2), &h2));
+  TRY(scratch(ctx, "arn_hcols", size_t(m) * (m + 1) * g.npad * sizeof(double2), &hcols));
+  TRY(scratch(ctx, "arn_nrm", size_t(m + 1) * g.npad * sizeof(double2), &nrm));
+  TRY(scratch(ctx, "arn_w", stride * eb, &W));
+  CK(cudaMemsetAsync(hcols, 0, size_t(m) * (m + 1) * g.npad * sizeof(double2), s));
+  char* Vb = reinterpret_cast<char*>(V);
+  double2* nrm2 = reinterpret_cast<double2*>(nrm);
+  // normalise the start vector: nrm[0] = ||v0||^2
+  CK(mmc::launch_multidot(prec, g, V, stride, 1, V, 0, spc, (double2*)part, s));
+  CK(mmc::launch_reduce((double2*)part, nbx, 1, g.npad, nrm2, 0, s));
+  CK(mmc::launch_normalise(prec, g, V, nrm2, V, s));
+  for (int j = 0; j < m; ++j) {
+    void* vj = Vb + size_t(j) * stride * eb;
+    TRY(op(vj, W));
+    double2* hc = reinterpret_cast<double2*>(hcols) + size_t(j) * (m + 1) * g.npad;
+    CK(mmc::launch_multidot(prec, g, V, stride, j + 1, W, 0, spc, (double2*)part, s));
+    CK(mmc::launch_reduce((double2*)part, nbx, j + 1, g.npad, (double2*)h1, 0, s));
+    CK(mmc::launch_basis_update(prec, g, V, stride, j + 1, (double2*)h1, W, s));
+    CK(mmc::launch_multidot(prec, g, V, stride, j + 1, W, 0, spc, (double2*)part, s));
+    CK(mmc::launch_reduce((double2*)part, nbx, j + 1, g.npad, (double2*)h2, 0, s));
+    CK(mmc::launch_basis_update(prec, g, V, stride, j + 1, (double2*)h2, W, s));
+    CK(mmc::launch_add2((double2*)h1, (double2*)h2, hc, (j + 1) * g.npad, s));
+    CK(mmc::launch_multidot(prec, g, W, stride, 1, W, 0, spc, (double2*)part, s));
+    CK(mmc::launch_reduce((double2*)part, nbx, 1, g.npad, nrm2 + size_t(j + 1) * g.npad, 0, s));
+    CK(mmc::launch_normalise(prec, g, W, nrm2 + size_t(j + 1) * g.npad, Vb + size_t(j + 1) * stride * eb, s));
+  }
+  std::vector<double2> hh(size_t(m) * (m + 1) * g.npad), nn(size_t(m + 1) * g.npad);
+  CK(cudaMemcpyAsync(hh.data(), hcols, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(nn.data(), nrm, nn.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out.H.assign(g.npad, CMat(m + 1, m));
+  out.beta.assign(g.npad, 0.0);
+  for (int r = 0; r < g.npad; ++r) {
+    out.beta[r] = std::sqrt(nn[r].x);
+    for (int j = 0; j < m; ++j) {
+      for (int i = 0; i <= j; ++i) {
+        double2 v = hh[(size_t(j) * (m + 1) + i) * g.npad + r];
+        out.H[r](i, j) = cd(v.x, v.y);
+      }
+      out.H[r](j + 1, j) = std::sqrt(nn[size_t(j + 1) * g.npad + r].x);
+    }
+  }
+  return MMC_OK;
+}
+
+// Operator for a single-vector FP64 Arnoldi: M, or phi_h(M) = M p_h(M).
+inline int apply_op_f64(mmc_ctx* ctx, int op_handle, const void* in, void* out, int nrhs, cudaStream_t s) {
+  if (op_handle == MMC_OP_M) return apply_M_impl(ctx, in, out, nrhs, MMC_F64, false, s);
+  void* T;
+  geom g = make_geom(ctx, nrhs);
+  TRY(scratch(ctx, "phi_tmp", field_bytes(g, MMC_F64), &T));
+  Run base;
+  base.g = g;
+  base.prec = MMC_F64;
+  TRY(apply_poly_impl(ctx, op_handle, in, nrhs, MMC_F64, ACC_Y, T, base, s));
+  return apply_M_impl(ctx, T, out, nrhs, MMC_F64, false, s);
+}
+
+inline int check_ctx(mmc_ctx* ctx) {
+  if (!ctx) return MMC_ERR_ARG;
+  if (!ctx->gauge) RET(MMC_ERR_STATE, "no gauge field loaded");
+  CK(cudaSetDevice(ctx->device));
+  return MMC_OK;
+}
+
+}  // namespace host
+}  // namespace mmc

@@ -1,0 +1,74 @@
+// Host-side declarations of the library's CUDA kernels (launch wrappers).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mmc {
+
+// Geometry of a blocked field batch: [rb][site][c][R], rb < nrb, npad = nrb * R.
+struct geom {
+  int V, R, nrb, npad;
+};
+
+// Fused stencil step (stencil.cu).  prec: 0 F64, 1 F32, 2 BF16; rpt: rhs per lane.
+cudaError_t launch_step(int prec, int rpt, const step_params& p, int n_rb, cudaStream_t s);
+
+// Z(4) noise (Sec. 1) into a field of precision prec and/or packed codes.
+// ids[r] = (level, noise index) for rhs r (npad entries, device); entries with
+// level == 0xffffffff give zero vectors (padding).
+cudaError_t launch_noise(int prec, geom g, const uint2* ids, uint32_t tag, uint64_t seed, void* field,
+                         uint32_t* codes, cudaStream_t s);
+
+// Probe vectors (Sec. 6 probing): rhs r has unit entries at component comp[r] on every
+// site of colour col[r] (colour table per site, n entries); value 0 elsewhere.
+cudaError_t launch_probe(int prec, geom g, const int* site_colour, const int2* probe, void* field,
+                         cudaStream_t s);
+
+// Canonical complex128 [rhs][site][12] (device) <-> blocked field of precision prec.
+cudaError_t launch_pack(int prec, geom g, int nrhs, const double2* canon, void* field, cudaStream_t s);
+cudaError_t launch_unpack(int prec, geom g, int nrhs, const void* field, double2* canon, cudaStream_t s);
+
+// dst (precision pd) = src (precision ps), same geometry.
+cudaError_t launch_convert(int pd, void* dst, int ps, const void* src, geom g, cudaStream_t s);
+
+// Per-rhs partial dots for a set of basis fields: partial[bx][i][npad] =
+// sum over the CTA's sites of conj(A_i) . w (optionally with Theta on w).
+// prec 0 (F64, double2 fields) or 1 (F32, float2 fields); spc sites per CTA.
+cudaError_t launch_multidot(int prec, geom g, const void* A, size_t a_stride, int nvec, const void* w,
+                            int theta, int spc, double2* partial, cudaStream_t s);
+// out[i][npad] = sum_bx partial[bx][i][npad] (+ out if accumulate).
+cudaError_t launch_reduce(const double2* partial, int nbx, int nvec, int npad, double2* out, int accumulate,
+                          cudaStream_t s);
+// w -= sum_i A_i * h[i][r] (h device, double2 [nvec][npad]).
+cudaError_t launch_basis_update(int prec, geom g, const void* A, size_t a_stride, int nvec, const double2* h,
+                                void* w, cudaStream_t s);
+// dst = scale(r) * src with scale = 1 / sqrt(nrm2[r].x), zero if nrm2 == 0.
+cudaError_t launch_normalise(int prec, geom g, const void* src, const double2* nrm2, void* dst, cudaStream_t s);
+// y = a[r] * x + b[r] * y (complex per-rhs coefficients on the device).
+cudaError_t launch_axpby(int prec, geom g, const double2* a, const void* x, const double2* b, void* y,
+                         cudaStream_t s);
+// Apply gamma_5 (theta = 2) or gamma_4 (theta = 1) site-locally: dst = Theta src.
+cudaError_t launch_gamma(int prec, geom g, int theta, const void* src, void* dst, cudaStream_t s);
+// Bilinear partials of Z(4) codes against a field: partial[bx][npad] += sum conj(eta) Theta x.
+cudaError_t launch_bilinear_codes(int prec, geom g, const uint32_t* codes, int theta, const void* x, int spc,
+                                  double2* partial, cudaStream_t s);
+
+// Deflation projections (Sec. 7) of noise codes against k FP64 single-vector fields:
+// a[i][r] = sum conj(eta_r) (Theta z_i),  b[i][r] = sum conj(u_i) eta_r  (partials per CTA).
+cudaError_t launch_defl_proj(geom g, const uint32_t* codes, int theta, const double2* Z, const double2* U,
+                             int k, int spc, double2* partial_a, double2* partial_b, cudaStream_t s);
+
+// Projections of a batch field on k single-vector FP64 fields v_i and the matching
+// update: partial[bx][i][npad] = sum conj(v_i) . f_r;  f_r += sum_i v_i coef[i][r].
+cudaError_t launch_vec_proj(int prec, geom g, const double2* Vv, int k, const void* f, int spc, double2* partial,
+                            cudaStream_t s);
+cudaError_t launch_vec_update(int prec, geom g, const double2* Vv, int k, const double2* coef, void* f,
+                              cudaStream_t s);
+
+// Complex small-matrix kernels on the device for the Arnoldi bookkeeping.
+// hcol[i] = h1[i] + h2[i] for i < n (per rhs), written into H column storage.
+cudaError_t launch_add2(const double2* a, const double2* b, double2* out, int n, cudaStream_t s);
+
+}  // namespace mmc

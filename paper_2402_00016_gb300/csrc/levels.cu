@@ -1,0 +1,626 @@
+// Deflation (Sec. 7, Sec. 8), refined deflated solves (Sec. 1, Sec. 8), Monte
+// Carlo levels (Eq. 2, Sec. 6, Sec. 7), exact traces by unit vectors or
+// probing (Sec. 6) and the probing colouring search.
+#include <array>
+#include <chrono>
+#include <numeric>
+#include <random>
+
+#include "internal.h"
+
+using namespace mmc::host;
+using mmc::cd;
+using mmc::CMat;
+using mmc::geom;
+
+namespace {
+
+const int kSpc = 256;  // sites per CTA of the reduction kernels
+
+// Sum the partials [nbx][nvec][npad] on the device and copy nvec x npad values to host.
+int reduce_to_host(mmc_ctx* ctx, const double2* partial, int nbx, int nvec, int npad, std::vector<cd>& out,
+                   cudaStream_t s) {
+  void* red;
+  TRY(scratch(ctx, "red_out", size_t(nvec) * npad * sizeof(double2), &red));
+  CK(mmc::launch_reduce(partial, nbx, nvec, npad, (double2*)red, 0, s));
+  std::vector<double2> h(size_t(nvec) * npad);
+  CK(cudaMemcpyAsync(h.data(), red, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out.resize(h.size());
+  for (size_t i = 0; i < h.size(); ++i) out[i] = cd(h[i].x, h[i].y);
+  return MMC_OK;
+}
+
+// Per-rhs squared norms of a field (prec 0 or 1).
+int norms2(mmc_ctx* ctx, int prec, const geom& g, const void* f, std::vector<double>& out, cudaStream_t s) {
+  const int nbx = (g.V + kSpc - 1) / kSpc;
+  void* part;
+  TRY(scratch(ctx, "n2_part", size_t(nbx) * g.npad * sizeof(double2), &part));
+  CK(mmc::launch_multidot(prec, g, f, 0, 1, f, 0, kSpc, (double2*)part, s));
+  std::vector<cd> v;
+  TRY(reduce_to_host(ctx, (double2*)part, nbx, 1, g.npad, v, s));
+  out.resize(g.npad);
+  for (int r = 0; r < g.npad; ++r) out[r] = v[r].real();
+  return MMC_OK;
+}
+
+int upload(mmc_ctx* ctx, const std::string& key, const std::vector<cd>& h, void** dev, cudaStream_t s) {
+  std::vector<double2> t(h.size());
+  for (size_t i = 0; i < h.size(); ++i) t[i] = make_double2(h[i].real(), h[i].imag());
+  TRY(scratch(ctx, key, std::max<size_t>(1, t.size()) * sizeof(double2), dev));
+  CK(cudaMemcpyAsync(*dev, t.data(), t.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // host staging vector goes out of scope
+  return MMC_OK;
+}
+
+// r = b - M x (FP64): one step launch with a = -1, b = kappa, g = 1 (aux = b).
+int residual_f64(mmc_ctx* ctx, const geom& g, const void* b, const void* x, void* r, cudaStream_t s) {
+  Run run;
+  run.g = g;
+  run.prec = MMC_F64;
+  Step st;
+  st.in = x;
+  st.out = r;
+  st.aux = b;
+  st.flags = mmc::SF_HOP | mmc::SF_WRITE | mmc::SF_AUX;
+  st.coef = coef_block(g.npad);
+  for (int i = 0; i < g.npad; ++i) set_coef(st.coef, g.npad, i, -1.0, ctx->kappa, 1.0, 0, 0);
+  run.steps.push_back(st);
+  return exec_run(ctx, run, s);
+}
+
+// ------------------------------------------------------------------ solves
+// x += Z Lambda^-1 U^H r for every rhs (oblique eigen-projection of the residual).
+int deflate_residual(mmc_ctx* ctx, const geom& g, const void* r, void* x, cudaStream_t s) {
+  const int k = ctx->k_defl;
+  if (k == 0) return MMC_OK;
+  const int nbx = (g.V + kSpc - 1) / kSpc;
+  void* part;
+  TRY(scratch(ctx, "dr_part", size_t(nbx) * k * g.npad * sizeof(double2), &part));
+  CK(mmc::launch_vec_proj(MMC_F64, g, ctx->U, k, r, kSpc, (double2*)part, s));
+  std::vector<cd> c;
+  TRY(reduce_to_host(ctx, (double2*)part, nbx, k, g.npad, c, s));
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < g.npad; ++j) c[size_t(i) * g.npad + j] /= ctx->lambda[i];
+  void* dc;
+  TRY(upload(ctx, "dr_coef", c, &dc, s));
+  CK(mmc::launch_vec_update(MMC_F64, g, ctx->Z, k, (const double2*)dc, x, s));
+  return MMC_OK;
+}
+
+int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int precond, int prec_inner, int m,
+               int max_outer, int* iters, std::vector<double>& rel, cudaStream_t s) {
+  const geom g = make_geom(ctx, nrhs);
+  const size_t f64 = field_bytes(g, MMC_F64), f32 = field_bytes(g, MMC_F32);
+  void *r, *r32, *Vb, *Zb, *e32, *e64;
+  TRY(scratch(ctx, "sv_r", f64, &r));
+  TRY(scratch(ctx, "sv_r32", f32, &r32));
+  TRY(scratch(ctx, "sv_V", f32 * (m + 1), &Vb));
+  if (precond != MMC_ZERO) TRY(scratch(ctx, "sv_Z", f32 * m, &Zb));
+  TRY(scratch(ctx, "sv_e32", f32, &e32));
+  TRY(scratch(ctx, "sv_e64", f64, &e64));
+  std::vector<double> bn2, rn2;
+  TRY(norms2(ctx, MMC_F64, g, b, bn2, s));
+  int inner = 0;
+  rel.assign(nrhs, 0.0);
+  const size_t stride32 = size_t(g.npad) * g.V * 12;
+  for (int outer = 0; outer <= max_outer; ++outer) {
+    TRY(residual_f64(ctx, g, b, x, r, s));
+    if (ctx->k_defl > 0) {
+      TRY(deflate_residual(ctx, g, r, x, s));
+      TRY(residual_f64(ctx, g, b, x, r, s));
+    }
+    TRY(norms2(ctx, MMC_F64, g, r, rn2, s));
+    bool done = true;
+    for (int i = 0; i < nrhs; ++i) {
+      if (!std::isfinite(rn2[i])) RET(MMC_ERR_NAN, "mmc_solve: NaN in the residual");
+      rel[i] = bn2[i] > 0 ? std::sqrt(rn2[i] / bn2[i]) : 0.0;
+      if (rel[i] > tol) done = false;
+    }
+    if (done) {
+      if (iters) *iters = inner;
+      return MMC_OK;
+    }
+    if (outer == max_outer) break;
+    // inner right-preconditioned FGMRES(m) cycle in FP32 on M e = r
+    CK(mmc::launch_convert(MMC_F32, Vb, MMC_F64, r, g, s));
+    auto op = [&](const void* vj, void* w) -> int {
+      const void* zj = vj;
+      if (precond != MMC_ZERO) {
+        const size_t j = (reinterpret_cast<const char*>(vj) - reinterpret_cast<const char*>(Vb)) / (stride32 * 8);
+        void* zdst = reinterpret_cast<char*>(Zb) + j * stride32 * 8;
+        Run base;
+        base.g = g;
+        if (prec_inner == MMC_BF16) {
+          void* v16;
+          void* y32;
+          TRY(scratch(ctx, "sv_v16", field_bytes(g, MMC_BF16), &v16));
+          TRY(scratch(ctx, "sv_y32", f32, &y32));
+          CK(mmc::launch_convert(MMC_BF16, v16, MMC_F32, vj, g, s));
+          base.prec = MMC_BF16;
+          TRY(apply_poly_impl(ctx, precond, v16, g.npad, MMC_BF16, ACC_Y, zdst, base, s));
+        } else {
+          base.prec = MMC_F32;
+          TRY(apply_poly_impl(ctx, precond, vj, g.npad, MMC_F32, ACC_Y, zdst, base, s));
+        }
+        zj = zdst;
+      }
+      return apply_M_impl(ctx, zj, w, g.npad, MMC_F32, false, s);
+    };
+    ArnoldiOut ao;
+    TRY(arnoldi_cgs2(ctx, g, MMC_F32, Vb, m, op, ao, s));
+    inner += m;
+    std::vector<cd> ycoef(size_t(m) * g.npad, cd(0, 0));
+    for (int rr = 0; rr < g.npad; ++rr) {
+      if (ao.beta[rr] == 0) continue;
+      std::vector<cd> rhs(m + 1, cd(0, 0));
+      rhs[0] = ao.beta[rr];
+      double res;
+      std::vector<cd> y = mmc::hessenberg_lstsq(ao.H[rr], m, rhs, &res);
+      for (int j = 0; j < m; ++j) ycoef[size_t(j) * g.npad + rr] = -y[j];  // basis_update subtracts
+    }
+    void* dy;
+    TRY(upload(ctx, "sv_y", ycoef, &dy, s));
+    CK(cudaMemsetAsync(e32, 0, f32, s));
+    CK(mmc::launch_basis_update(MMC_F32, g, precond != MMC_ZERO ? Zb : Vb, stride32, m, (const double2*)dy, e32, s));
+    CK(mmc::launch_convert(MMC_F64, e64, MMC_F32, e32, g, s));
+    std::vector<cd> one(g.npad, cd(1, 0));
+    void* d1;
+    TRY(upload(ctx, "sv_one", one, &d1, s));
+    CK(mmc::launch_axpby(MMC_F64, g, (const double2*)d1, e64, (const double2*)d1, x, s));
+  }
+  if (iters) *iters = inner;
+  RET(MMC_ERR_NOCONV, "mmc_solve: relative residual above tolerance after max_outer cycles");
+}
+
+// ------------------------------------------------------------- colouring
+// Lattice colourings c(x) = sum_k ((a_k . x) mod q_k) * stride_k with q_k | gcd(L):
+// same-colour displacements form a sublattice; valid when no displacement of
+// periodic L1 norm 1..reach lies in it.
+struct Colouring {
+  int n = 0;
+  std::vector<int> colour;  // per site
+};
+
+void displacements(const int* L, int reach, std::vector<std::array<int, 4>>& out) {
+  out.clear();
+  int lo[4], hi[4];
+  for (int m = 0; m < 4; ++m) {
+    hi[m] = std::min(reach, L[m] / 2);
+    lo[m] = -std::min(reach, (L[m] - 1) / 2);
+  }
+  for (int a = lo[0]; a <= hi[0]; ++a)
+    for (int b = lo[1]; b <= hi[1]; ++b)
+      for (int c = lo[2]; c <= hi[2]; ++c)
+        for (int d = lo[3]; d <= hi[3]; ++d) {
+          int n1 = std::abs(a) + std::abs(b) + std::abs(c) + std::abs(d);
+          if (n1 == 0 || n1 > reach) continue;
+          out.push_back({a, b, c, d});
+        }
+}
+
+Colouring find_colouring(const int* L, int V, int reach) {
+  Colouring col;
+  if (reach <= 0) {
+    col.n = 1;
+    col.colour.assign(V, 0);
+    return col;
+  }
+  int G = L[0];
+  for (int m = 1; m < 4; ++m) G = std::gcd(G, L[m]);
+  std::vector<std::array<int, 4>> D;
+  displacements(L, reach, D);
+  // candidate moduli tuples, by number of colours
+  std::vector<int> divs;
+  for (int q = 2; q <= G; ++q)
+    if (G % q == 0) divs.push_back(q);
+  struct Cand {
+    std::vector<int> q;
+    long long n;
+  };
+  std::vector<Cand> cands;
+  for (int q1 : divs) {
+    cands.push_back({{q1}, q1});
+    for (int q2 : divs) {
+      if (q2 > q1) continue;
+      cands.push_back({{q1, q2}, (long long)q1 * q2});
+      for (int q3 : divs) {
+        if (q3 > q2) continue;
+        cands.push_back({{q1, q2, q3}, (long long)q1 * q2 * q3});
+      }
+    }
+  }
+  std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.n < b.n; });
+  const long long lower = (long long)D.size() / 8;  // cheap lower bound: skip hopeless tiny counts
+  std::mt19937 rng(12345);
+  for (const Cand& c : cands) {
+    if (c.n >= V || c.n < lower) continue;
+    const int K = int(c.q.size());
+    for (int trial = 0; trial < 4000; ++trial) {
+      int a[3][4];
+      for (int k = 0; k < K; ++k)
+        for (int m = 0; m < 4; ++m) a[k][m] = int(rng() % c.q[k]);
+      bool ok = true;
+      for (auto& d : D) {
+        bool sep = false;
+        for (int k = 0; k < K && !sep; ++k) {
+          long long v = 0;
+          for (int m = 0; m < 4; ++m) v += (long long)a[k][m] * d[m];
+          if (((v % c.q[k]) + c.q[k]) % c.q[k] != 0) sep = true;
+        }
+        if (!sep) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) continue;
+      col.n = int(c.n);
+      col.colour.resize(V);
+      for (int s = 0; s < V; ++s) {
+        int x[4] = {s % L[0], (s / L[0]) % L[1], (s / (L[0] * L[1])) % L[2], s / (L[0] * L[1] * L[2])};
+        int cc = 0, stride = 1;
+        for (int k = 0; k < K; ++k) {
+          long long v = 0;
+          for (int m = 0; m < 4; ++m) v += (long long)a[k][m] * x[m];
+          cc += int(v % c.q[k]) * stride;
+          stride *= c.q[k];
+        }
+        col.colour[s] = cc;
+      }
+      return col;
+    }
+  }
+  col.n = V;  // fall back to unit vectors: every site its own colour
+  col.colour.resize(V);
+  std::iota(col.colour.begin(), col.colour.end(), 0);
+  return col;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_accept, double* lambda_out,
+                int* k_accepted) {
+  TRY(check_ctx(ctx));
+  if (k < 1 || m_arn < 2 || !k_accepted) RET(MMC_ERR_ARG, "mmc_deflate: bad argument");
+  if (poly_handle != MMC_OP_M &&
+      (!valid_poly(ctx, poly_handle) || ctx->polys[poly_handle].kind != 0 || ctx->polys[poly_handle].op != MMC_OP_M))
+    RET(MMC_ERR_ARG, "mmc_deflate: poly_handle must be a single polynomial in M");
+  cudaStream_t s = ctx->stream;
+  const geom g = make_geom(ctx, 1);
+  const size_t fb = field_bytes(g, MMC_F64);
+  const size_t n = size_t(ctx->V) * 12;
+  void *V;
+  TRY(scratch(ctx, "df_V", fb * (m_arn + 1), &V));
+  std::vector<uint2> ids(1, make_uint2(0u, 0u));
+  void* dids;
+  TRY(scratch(ctx, "ids", sizeof(uint2), &dids));
+  CK(cudaMemcpyAsync(dids, ids.data(), sizeof(uint2), cudaMemcpyHostToDevice, s));
+  CK(mmc::launch_noise(MMC_F64, g, (const uint2*)dids, MMC_TAG_ARNOLDI, ctx->seed, V, nullptr, s));
+  ArnoldiOut ao;
+  auto op = [&](const void* in, void* out) { return apply_op_f64(ctx, poly_handle, in, out, 1, s); };
+  TRY(arnoldi_cgs2(ctx, g, MMC_F64, V, m_arn, op, ao, s));
+  CMat Hm(m_arn, m_arn);
+  for (int j = 0; j < m_arn; ++j)
+    for (int i = 0; i < m_arn; ++i) Hm(i, j) = ao.H[0](i, j);
+  std::vector<cd> mu;
+  CMat G;
+  if (!mmc::eig(Hm, mu, &G)) RET(MMC_ERR_NOCONV, "mmc_deflate: Ritz eigenproblem did not converge");
+  // every Ritz vector z = V_m g, its Rayleigh quotient on M and residual
+  void *Zc, *MZ, *Rv, *part;
+  TRY(scratch(ctx, "df_Zc", fb * m_arn, &Zc));
+  TRY(scratch(ctx, "df_MZ", fb, &MZ));
+  TRY(scratch(ctx, "df_R", fb, &Rv));
+  const int nbx = (g.V + kSpc - 1) / kSpc;
+  TRY(scratch(ctx, "df_part", size_t(nbx) * std::max(m_arn, k) * sizeof(double2), &part));
+  std::vector<cd> lam(m_arn);
+  std::vector<double> res(m_arn);
+  for (int i = 0; i < m_arn; ++i) {
+    std::vector<cd> h(m_arn);
+    for (int j = 0; j < m_arn; ++j) h[j] = -G(j, i);
+    void* dh;
+    TRY(upload(ctx, "df_h", h, &dh, s));
+    char* zi = reinterpret_cast<char*>(Zc) + size_t(i) * fb;
+    CK(cudaMemsetAsync(zi, 0, fb, s));
+    CK(mmc::launch_basis_update(MMC_F64, g, V, n, m_arn, (const double2*)dh, zi, s));
+    std::vector<double> nz;
+    TRY(norms2(ctx, MMC_F64, g, zi, nz, s));
+    std::vector<cd> sc(1, cd(1.0 / std::sqrt(nz[0]), 0));
+    void* dsc;
+    TRY(upload(ctx, "df_sc", sc, &dsc, s));
+    CK(mmc::launch_axpby(MMC_F64, g, (const double2*)dsc, zi, nullptr, zi, s));
+    TRY(apply_M_impl(ctx, zi, MZ, 1, MMC_F64, false, s));
+    CK(mmc::launch_multidot(MMC_F64, g, zi, 0, 1, MZ, 0, kSpc, (double2*)part, s));
+    std::vector<cd> l;
+    TRY(reduce_to_host(ctx, (double2*)part, nbx, 1, 1, l, s));
+    lam[i] = l[0];
+    std::vector<cd> ca(1, -lam[i]), cb(1, cd(1, 0));
+    void *dca, *dcb;
+    TRY(upload(ctx, "df_ca", ca, &dca, s));
+    TRY(upload(ctx, "df_cb", cb, &dcb, s));
+    CK(cudaMemcpyAsync(Rv, MZ, fb, cudaMemcpyDeviceToDevice, s));
+    CK(mmc::launch_axpby(MMC_F64, g, (const double2*)dca, zi, (const double2*)dcb, Rv, s));
+    std::vector<double> rn;
+    TRY(norms2(ctx, MMC_F64, g, Rv, rn, s));
+    res[i] = std::sqrt(rn[0]);
+  }
+  std::vector<int> acc;
+  for (int i = 0; i < m_arn; ++i)
+    if (res[i] < tol_accept && std::isfinite(res[i])) acc.push_back(i);
+  std::stable_sort(acc.begin(), acc.end(), [&](int a, int b) { return std::abs(lam[a]) < std::abs(lam[b]); });
+  if (int(acc.size()) > k) acc.resize(k);
+  // left vectors from gamma5-hermiticity: partner with conj(lambda), |Im| < 2e-4 counts as real
+  const double real_tol = 2e-4;
+  std::vector<int> keep, partner;
+  for (size_t a = 0; a < acc.size(); ++a) {
+    cd l = lam[acc[a]];
+    if (std::abs(l.imag()) < real_tol) {
+      keep.push_back(acc[a]);
+      partner.push_back(acc[a]);
+      continue;
+    }
+    int best = -1;
+    double bd = 1e300;
+    for (size_t b2 = 0; b2 < acc.size(); ++b2) {
+      if (b2 == a) continue;
+      double d = std::abs(lam[acc[b2]] - std::conj(l));
+      if (d < bd) {
+        bd = d;
+        best = acc[b2];
+      }
+    }
+    if (best >= 0 && bd < std::max(real_tol, 1e-6 * std::abs(l)) * 10) {
+      keep.push_back(acc[a]);
+      partner.push_back(best);
+    }
+  }
+  const int kk = int(keep.size());
+  if (ctx->Z) cudaFree(ctx->Z);
+  if (ctx->U) cudaFree(ctx->U);
+  ctx->Z = ctx->U = nullptr;
+  ctx->k_defl = 0;
+  ctx->lambda.clear();
+  if (kk > 0) {
+    CK(cudaMalloc(&ctx->Z, fb * kk));
+    CK(cudaMalloc(&ctx->U, fb * kk));
+    void* W;
+    TRY(scratch(ctx, "df_W", fb * kk, &W));
+    for (int i = 0; i < kk; ++i) {
+      CK(cudaMemcpyAsync(reinterpret_cast<char*>(ctx->Z) + size_t(i) * fb,
+                         reinterpret_cast<char*>(Zc) + size_t(keep[i]) * fb, fb, cudaMemcpyDeviceToDevice, s));
+      CK(mmc::launch_gamma(MMC_F64, g, 2, reinterpret_cast<char*>(Zc) + size_t(partner[i]) * fb,
+                           reinterpret_cast<char*>(W) + size_t(i) * fb, s));
+    }
+    // S = W^H Z (kk x kk), U = W S^{-H}
+    CMat S(kk, kk);
+    for (int j = 0; j < kk; ++j) {
+      CK(mmc::launch_multidot(MMC_F64, g, W, n, kk, reinterpret_cast<char*>(ctx->Z) + size_t(j) * fb, 0, kSpc,
+                              (double2*)part, s));
+      std::vector<cd> col;
+      TRY(reduce_to_host(ctx, (double2*)part, nbx, kk, 1, col, s));
+      for (int i = 0; i < kk; ++i) S(i, j) = col[i];
+    }
+    CMat SH(kk, kk), Inv(kk, kk);
+    for (int i = 0; i < kk; ++i)
+      for (int j = 0; j < kk; ++j) SH(i, j) = std::conj(S(j, i));
+    for (int i = 0; i < kk; ++i) Inv(i, i) = 1.0;
+    if (!mmc::lu_solve(SH, Inv)) RET(MMC_ERR_BREAKDOWN, "mmc_deflate: W^H Z is singular");
+    // Inv = S^{-H};  U_i = sum_j W_j Inv(j, i)
+    for (int i = 0; i < kk; ++i) {
+      std::vector<cd> h(kk);
+      for (int j = 0; j < kk; ++j) h[j] = -Inv(j, i);
+      void* dh;
+      TRY(upload(ctx, "df_h", h, &dh, s));
+      char* ui = reinterpret_cast<char*>(ctx->U) + size_t(i) * fb;
+      CK(cudaMemsetAsync(ui, 0, fb, s));
+      CK(mmc::launch_basis_update(MMC_F64, g, W, n, kk, (const double2*)dh, ui, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < kk; ++i) ctx->lambda.push_back(lam[keep[i]]);
+    ctx->k_defl = kk;
+  }
+  *k_accepted = kk;
+  if (lambda_out)
+    for (int i = 0; i < kk; ++i) {
+      lambda_out[2 * i] = ctx->lambda[i].real();
+      lambda_out[2 * i + 1] = ctx->lambda[i].imag();
+    }
+  return MMC_OK;
+}
+
+int mmc_solve(mmc_ctx* ctx, const void* b, void* x, int nrhs, double rel_tol, int precond, int prec_inner,
+              int m_inner, int max_outer, int* iters, double* relres_out) {
+  TRY(check_ctx(ctx));
+  if (!b || !x || b == x || nrhs < 1 || m_inner < 1 || max_outer < 0 || !(rel_tol > 0))
+    RET(MMC_ERR_ARG, "mmc_solve: bad argument");
+  if (prec_inner != MMC_F32 && prec_inner != MMC_BF16) RET(MMC_ERR_ARG, "mmc_solve: prec_inner must be F32 or BF16");
+  if (precond != MMC_ZERO && !valid_poly(ctx, precond)) RET(MMC_ERR_ARG, "mmc_solve: bad preconditioner handle");
+  std::vector<double> rel;
+  int rc = solve_impl(ctx, b, x, nrhs, rel_tol, precond, prec_inner, m_inner, max_outer, iters, rel, ctx->stream);
+  if (relres_out)
+    for (int i = 0; i < nrhs && i < int(rel.size()); ++i) relres_out[i] = rel[i];
+  CK(cudaStreamSynchronize(ctx->stream));
+  return rc;
+}
+
+int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int n_noise, uint32_t first,
+                    uint32_t level, int prec, int precond, mmc_level_stats* out, double* samples_out) {
+  TRY(check_ctx(ctx));
+  if (!out || n_noise < 1 || prec < 0 || prec > 2 || theta_op < 0 || theta_op > 2)
+    RET(MMC_ERR_ARG, "mmc_trace_level: bad argument");
+  if (!(hi == MMC_INV || valid_poly(ctx, hi)) || !(lo == MMC_ZERO || valid_poly(ctx, lo)))
+    RET(MMC_ERR_ARG, "mmc_trace_level: bad level operands");
+  const auto t0 = std::chrono::steady_clock::now();
+  const long long mv0 = ctx->matvecs;
+  cudaStream_t s = ctx->stream;
+  const geom g = make_geom(ctx, n_noise);
+  const int nbx = nbx_for(ctx, ctx->spc_step);
+  void *codes, *X, *part, *dids;
+  TRY(scratch(ctx, "lv_codes", size_t(g.npad) * g.V * sizeof(uint32_t), &codes));
+  TRY(scratch(ctx, "lv_X", field_bytes(g, prec), &X));
+  TRY(scratch(ctx, "lv_part", size_t(std::max(nbx, (g.V + kSpc - 1) / kSpc)) * g.npad * sizeof(double2), &part));
+  std::vector<uint2> ids(g.npad);
+  for (int r = 0; r < g.npad; ++r) ids[r] = r < n_noise ? make_uint2(level, first + r) : make_uint2(0xffffffffu, 0);
+  TRY(scratch(ctx, "lv_ids", ids.size() * sizeof(uint2), &dids));
+  CK(cudaMemcpyAsync(dids, ids.data(), ids.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+  CK(mmc::launch_noise(prec, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, X, (uint32_t*)codes, s));
+  std::vector<cd> x(g.npad, cd(0, 0));
+  auto poly_bilinear = [&](int h, double sign) -> int {
+    CK(cudaMemsetAsync(part, 0, size_t(nbx) * g.npad * sizeof(double2), s));
+    Run base;
+    base.g = g;
+    base.prec = prec;
+    base.codes = (const uint32_t*)codes;
+    base.theta = theta_op;
+    base.partial = (double2*)part;
+    base.nbx = nbx;
+    TRY(apply_poly_impl(ctx, h, X, n_noise, prec, ACC_BIL, nullptr, base, s));
+    std::vector<cd> v;
+    TRY(reduce_to_host(ctx, (double2*)part, nbx, 1, g.npad, v, s));
+    for (int r = 0; r < g.npad; ++r) x[r] += sign * v[r];
+    return MMC_OK;
+  };
+  if (hi == MMC_INV) {
+    void *b64, *x64;
+    TRY(scratch(ctx, "lv_b64", field_bytes(g, MMC_F64), &b64));
+    TRY(scratch(ctx, "lv_x64", field_bytes(g, MMC_F64), &x64));
+    CK(mmc::launch_noise(MMC_F64, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, b64, nullptr, s));
+    CK(cudaMemsetAsync(x64, 0, field_bytes(g, MMC_F64), s));
+    std::vector<double> rel;
+    int its = 0;
+    TRY(solve_impl(ctx, b64, x64, n_noise, 1e-10, precond, MMC_F32, 48, 400, &its, rel, s));
+    const int nb2 = (g.V + kSpc - 1) / kSpc;
+    CK(cudaMemsetAsync(part, 0, size_t(nb2) * g.npad * sizeof(double2), s));
+    CK(mmc::launch_bilinear_codes(MMC_F64, g, (const uint32_t*)codes, theta_op, x64, kSpc, (double2*)part, s));
+    std::vector<cd> v;
+    TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, g.npad, v, s));
+    for (int r = 0; r < g.npad; ++r) x[r] += v[r];
+  } else {
+    TRY(poly_bilinear(hi, 1.0));
+  }
+  if (lo != MMC_ZERO) TRY(poly_bilinear(lo, -1.0));
+  cd corr(0, 0);
+  int kd = 0;
+  if (deflate && hi != MMC_INV && ctx->k_defl > 0) {
+    const int k = ctx->k_defl;
+    kd = k;
+    const geom g1 = make_geom(ctx, 1);
+    const int nb2 = (g.V + kSpc - 1) / kSpc;
+    void *pa, *pb;
+    TRY(scratch(ctx, "lv_pa", size_t(nb2) * k * g.npad * sizeof(double2), &pa));
+    TRY(scratch(ctx, "lv_pb", size_t(nb2) * k * g.npad * sizeof(double2), &pb));
+    CK(mmc::launch_defl_proj(g, (const uint32_t*)codes, theta_op, ctx->Z, ctx->U, k, kSpc, (double2*)pa, (double2*)pb,
+                             s));
+    std::vector<cd> A, B;
+    TRY(reduce_to_host(ctx, (double2*)pa, nb2, k, g.npad, A, s));
+    TRY(reduce_to_host(ctx, (double2*)pb, nb2, k, g.npad, B, s));
+    const size_t n = size_t(ctx->V) * 12;
+    for (int i = 0; i < k; ++i) {
+      cd c = poly_value(ctx, hi, ctx->lambda[i]) - (lo == MMC_ZERO ? cd(0, 0) : poly_value(ctx, lo, ctx->lambda[i]));
+      for (int r = 0; r < n_noise; ++r) x[r] -= c * A[size_t(i) * g.npad + r] * B[size_t(i) * g.npad + r];
+      CK(mmc::launch_multidot(MMC_F64, g1, ctx->U + size_t(i) * n, 0, 1, ctx->Z + size_t(i) * n, theta_op, kSpc,
+                              (double2*)part, s));
+      std::vector<cd> d;
+      TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, 1, d, s));
+      corr += c * d[0];
+    }
+  }
+  // statistics (Sec. 4, Sec. 8 readings: unbiased variance of each part, stderr = s / sqrt(N))
+  cd mean(0, 0);
+  for (int r = 0; r < n_noise; ++r) mean += x[r];
+  mean /= double(n_noise);
+  double vr = 0, vi = 0, cv = 0;
+  for (int r = 0; r < n_noise; ++r) {
+    cd d = x[r] - mean;
+    vr += d.real() * d.real();
+    vi += d.imag() * d.imag();
+    cv += std::norm(d);
+  }
+  const double dn = n_noise > 1 ? double(n_noise - 1) : 1.0;
+  std::memset(out, 0, sizeof(*out));
+  out->n = n_noise;
+  out->k_deflated = kd;
+  out->mean_re = mean.real();
+  out->mean_im = mean.imag();
+  out->var_re = n_noise > 1 ? vr / dn : 0.0;
+  out->var_im = n_noise > 1 ? vi / dn : 0.0;
+  out->cvar = n_noise > 1 ? cv / dn : 0.0;
+  out->stderr_re = std::sqrt(out->var_re / n_noise);
+  out->stderr_im = std::sqrt(out->var_im / n_noise);
+  out->corr_re = corr.real();
+  out->corr_im = corr.imag();
+  out->value_re = mean.real() + corr.real();
+  out->value_im = mean.imag() + corr.imag();
+  out->matvecs = ctx->matvecs - mv0;
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (samples_out)
+    for (int r = 0; r < n_noise; ++r) {
+      samples_out[2 * r] = x[r].real();
+      samples_out[2 * r + 1] = x[r].imag();
+    }
+  for (int r = 0; r < n_noise; ++r)
+    if (!std::isfinite(x[r].real()) || !std::isfinite(x[r].imag())) RET(MMC_ERR_NAN, "mmc_trace_level: NaN sample");
+  return MMC_OK;
+}
+
+int mmc_probe_colours(mmc_ctx* ctx, int reach, int* n_colours) {
+  if (!ctx || reach < 0 || !n_colours) return MMC_ERR_ARG;
+  Colouring c = find_colouring(ctx->dims, ctx->V, reach);
+  *n_colours = c.n;
+  return MMC_OK;
+}
+
+int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec, double* out) {
+  TRY(check_ctx(ctx));
+  if (!valid_poly(ctx, handle) || !out || prec < 0 || prec > 2 || theta_op < 0 || theta_op > 2)
+    RET(MMC_ERR_ARG, "mmc_trace_exact: bad argument");
+  cudaStream_t s = ctx->stream;
+  Colouring col;
+  if (method == MMC_EXACT_PROBE) {
+    col = find_colouring(ctx->dims, ctx->V, poly_degree(ctx, handle));
+  } else {
+    col.n = ctx->V;
+    col.colour.resize(ctx->V);
+    std::iota(col.colour.begin(), col.colour.end(), 0);
+  }
+  const long long nprobe = (long long)col.n * 12;
+  const int batch = int(std::min<long long>(nprobe, 256));
+  const geom g = make_geom(ctx, batch);
+  const int nbx = nbx_for(ctx, ctx->spc_step);
+  void *dcol, *dpr, *X, *part;
+  TRY(scratch(ctx, "ex_col", size_t(ctx->V) * sizeof(int), &dcol));
+  CK(cudaMemcpyAsync(dcol, col.colour.data(), size_t(ctx->V) * sizeof(int), cudaMemcpyHostToDevice, s));
+  TRY(scratch(ctx, "ex_pr", size_t(g.npad) * sizeof(int2), &dpr));
+  TRY(scratch(ctx, "ex_X", field_bytes(g, prec), &X));
+  TRY(scratch(ctx, "ex_part", size_t(nbx) * g.npad * sizeof(double2), &part));
+  CK(cudaMemsetAsync(part, 0, size_t(nbx) * g.npad * sizeof(double2), s));
+  std::vector<int2> pr(g.npad);
+  for (long long p0 = 0; p0 < nprobe; p0 += batch) {
+    int nb = int(std::min<long long>(batch, nprobe - p0));
+    for (int r = 0; r < g.npad; ++r) {
+      long long pidx = p0 + r;
+      pr[r] = (r < nb) ? make_int2(int(pidx / 12), int(pidx % 12)) : make_int2(-1, 0);
+    }
+    CK(cudaMemcpyAsync(dpr, pr.data(), pr.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    CK(mmc::launch_probe(prec, g, (const int*)dcol, (const int2*)dpr, X, s));
+    Run base;
+    base.g = g;
+    base.prec = prec;
+    base.left = X;
+    base.theta = theta_op;
+    base.partial = (double2*)part;
+    base.nbx = nbx;
+    TRY(apply_poly_impl(ctx, handle, X, g.npad, prec, ACC_BIL, nullptr, base, s));
+    CK(cudaStreamSynchronize(s));  // probe table is rewritten by the next batch
+  }
+  std::vector<cd> v;
+  TRY(reduce_to_host(ctx, (double2*)part, nbx, 1, g.npad, v, s));
+  cd tot(0, 0);
+  for (auto& z : v) tot += z;
+  out[0] = tot.real();
+  out[1] = tot.imag();
+  return MMC_OK;
+}
+
+}  // extern "C"

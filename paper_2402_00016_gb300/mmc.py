@@ -1,0 +1,283 @@
+"""Thin Python binding of the C ABI in include/mmc.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Device fields are
+torch uint8 tensors on the context's device (see ``new_field``); host arrays
+are numpy complex128 in the canonical order.  There is no CPU fallback: if
+libmmc.so cannot be loaded, importing this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmmc.so")
+
+MMC_OK = 0
+MMC_F64, MMC_F32, MMC_BF16 = 0, 1, 2
+MMC_THETA_ONE, MMC_THETA_G4, MMC_THETA_G5 = 0, 1, 2
+MMC_EXACT_UNIT, MMC_EXACT_PROBE = 0, 1
+MMC_OP_M = -1
+MMC_ZERO = -1
+MMC_INV = -2
+MMC_TAG_NOISE = 0x4E4F4953
+MMC_TAG_GMRES = 0x474D5253
+MMC_TAG_ARNOLDI = 0x4445464C
+PREC = {"f64": MMC_F64, "f32": MMC_F32, "bf16": MMC_BF16}
+THETA = {"1": MMC_THETA_ONE, "g4": MMC_THETA_G4, "g5": MMC_THETA_G5}
+ERRORS = {-1: "MMC_ERR_ARG", -2: "MMC_ERR_NOMEM", -3: "MMC_ERR_CUDA", -4: "MMC_ERR_BREAKDOWN",
+          -5: "MMC_ERR_NOCONV", -6: "MMC_ERR_TIMEOUT", -7: "MMC_ERR_NAN", -8: "MMC_ERR_STATE"}
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError("libmmc.so is not built (run __graft_entry__.build() or paper_2402_00016_gb300/build.py)")
+lib = ctypes.CDLL(_LIB_PATH)
+
+_vp, _i, _d, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint32,
+                                ctypes.c_uint64, ctypes.c_size_t)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class mmc_level_stats(ctypes.Structure):
+    _fields_ = [("n", _i), ("k_deflated", _i), ("mean_re", _d), ("mean_im", _d), ("var_re", _d),
+                ("var_im", _d), ("cvar", _d), ("stderr_re", _d), ("stderr_im", _d), ("corr_re", _d),
+                ("corr_im", _d), ("value_re", _d), ("value_im", _d), ("seconds", _d),
+                ("matvecs", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_SIGS = {
+    "mmc_create": (_i, [ctypes.POINTER(_vp), _ip, _u64, _i]),
+    "mmc_destroy": (_i, [_vp]),
+    "mmc_last_error": (ctypes.c_char_p, [_vp]),
+    "mmc_set_seed": (_i, [_vp, _u64]),
+    "mmc_rhs_block": (_i, [_i]),
+    "mmc_field_bytes": (_sz, [_vp, _i, _i]),
+    "mmc_load_gauge": (_i, [_vp, _dp, _d, _i]),
+    "mmc_pack": (_i, [_vp, _dp, _i, _i, _vp]),
+    "mmc_unpack": (_i, [_vp, _vp, _i, _i, _dp]),
+    "mmc_apply_M": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "mmc_noise": (_i, [_vp, _u32, _u32, _u32, _i, _i, _vp, _vp]),
+    "mmc_gmres_poly": (_i, [_vp, _i, _i, _dp, _ip]),
+    "mmc_poly_from_roots": (_i, [_vp, _i, _dp, _ip]),
+    "mmc_poly_double": (_i, [_vp, _i, _i, _ip]),
+    "mmc_poly_degree": (_i, [_vp, _i]),
+    "mmc_poly_eval": (_i, [_vp, _i, _i, _dp, _dp]),
+    "mmc_apply_poly": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
+    "mmc_deflate": (_i, [_vp, _i, _i, _i, _d, _dp, _ip]),
+    "mmc_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _i, _ip, _dp]),
+    "mmc_trace_level": (_i, [_vp, _i, _i, _i, _i, _i, _u32, _u32, _i, _i,
+                             ctypes.POINTER(mmc_level_stats), _dp]),
+    "mmc_trace_exact": (_i, [_vp, _i, _i, _i, _i, _dp]),
+    "mmc_probe_colours": (_i, [_vp, _i, _ip]),
+    "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
+    "mmc_leja_order": (_i, [_i, _dp, _dp]),
+    "mmc_eig": (_i, [_i, _dp, _i, _dp, _dp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class MMCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "error"), code, msg))
+        self.code = code
+
+
+def _check(code, ctx=None):
+    if code != MMC_OK:
+        msg = lib.mmc_last_error(ctx).decode() if ctx else ""
+        raise MMCError(code, msg)
+
+
+def _cplx(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(stream))
+
+
+# ------------------------------------------------------------------ context
+def mmc_create(dims, seed=0, device=0):
+    ctx = _vp()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    _check(lib.mmc_create(ctypes.byref(ctx), d, int(seed), int(device)))
+    return ctx
+
+
+def mmc_destroy(ctx):
+    _check(lib.mmc_destroy(ctx))
+
+
+def mmc_last_error(ctx):
+    return lib.mmc_last_error(ctx).decode()
+
+
+def mmc_set_seed(ctx, seed):
+    _check(lib.mmc_set_seed(ctx, int(seed)), ctx)
+
+
+def mmc_rhs_block(nrhs):
+    return lib.mmc_rhs_block(int(nrhs))
+
+
+def mmc_field_bytes(ctx, nrhs, prec):
+    return lib.mmc_field_bytes(ctx, int(nrhs), int(prec))
+
+
+def new_field(ctx, nrhs, prec, device="cuda"):
+    """A zeroed device field (torch uint8 tensor) for nrhs vectors of precision prec."""
+    import torch
+    return torch.zeros(mmc_field_bytes(ctx, nrhs, prec), dtype=torch.uint8, device=device)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if hasattr(t, "data_ptr") else ctypes.c_void_p(int(t))
+
+
+# ----------------------------------------------------------------- operator
+def mmc_load_gauge(ctx, U, kappa, t_antiperiodic=1):
+    U, p = _cplx(U)
+    _check(lib.mmc_load_gauge(ctx, p, float(kappa), int(t_antiperiodic)), ctx)
+
+
+def mmc_pack(ctx, host, nrhs, prec, field):
+    host, p = _cplx(host)
+    _check(lib.mmc_pack(ctx, p, int(nrhs), int(prec), _ptr(field)), ctx)
+
+
+def mmc_unpack(ctx, field, nrhs, prec, vol):
+    out = np.empty(int(nrhs) * int(vol) * 12, dtype=np.complex128)
+    _check(lib.mmc_unpack(ctx, _ptr(field), int(nrhs), int(prec), out.ctypes.data_as(_dp)), ctx)
+    return out.reshape(int(nrhs), int(vol) * 12)
+
+
+def mmc_apply_M(ctx, x, y, nrhs, prec, dagger=0, stream=None):
+    _check(lib.mmc_apply_M(ctx, _ptr(x), _ptr(y), int(nrhs), int(prec), int(dagger), _stream(stream)), ctx)
+
+
+def mmc_noise(ctx, level, first, tag, nrhs, prec, field, stream=None):
+    _check(lib.mmc_noise(ctx, int(level), int(first), int(tag), int(nrhs), int(prec), _ptr(field),
+                         _stream(stream)), ctx)
+
+
+# --------------------------------------------------------------- polynomials
+def mmc_gmres_poly(ctx, m, op_handle=MMC_OP_M):
+    theta = np.zeros(2 * int(m))
+    h = ctypes.c_int()
+    _check(lib.mmc_gmres_poly(ctx, int(m), int(op_handle), theta.ctypes.data_as(_dp), ctypes.byref(h)), ctx)
+    return h.value, theta[0::2] + 1j * theta[1::2]
+
+
+def mmc_poly_from_roots(ctx, theta):
+    theta, p = _cplx(theta)
+    h = ctypes.c_int()
+    _check(lib.mmc_poly_from_roots(ctx, int(theta.size), p, ctypes.byref(h)), ctx)
+    return h.value
+
+
+def mmc_poly_double(ctx, h_in, h_out):
+    h = ctypes.c_int()
+    _check(lib.mmc_poly_double(ctx, int(h_in), int(h_out), ctypes.byref(h)), ctx)
+    return h.value
+
+
+def mmc_poly_degree(ctx, handle):
+    d = lib.mmc_poly_degree(ctx, int(handle))
+    if d < 0:
+        _check(d, ctx)
+    return d
+
+
+def mmc_poly_eval(ctx, handle, alpha):
+    alpha, p = _cplx(np.atleast_1d(alpha))
+    out = np.zeros(alpha.size, dtype=np.complex128)
+    _check(lib.mmc_poly_eval(ctx, int(handle), int(alpha.size), p, out.ctypes.data_as(_dp)), ctx)
+    return out
+
+
+def mmc_apply_poly(ctx, handle, x, y, nrhs, prec, stream=None):
+    _check(lib.mmc_apply_poly(ctx, int(handle), _ptr(x), _ptr(y), int(nrhs), int(prec), _stream(stream)), ctx)
+
+
+# -------------------------------------------------------- deflation / solves
+def mmc_deflate(ctx, k, poly_handle, m_arnoldi, tol_accept=1e-3):
+    lam = np.zeros(2 * int(k))
+    ka = ctypes.c_int()
+    _check(lib.mmc_deflate(ctx, int(k), int(poly_handle), int(m_arnoldi), float(tol_accept),
+                           lam.ctypes.data_as(_dp), ctypes.byref(ka)), ctx)
+    return (lam[0::2] + 1j * lam[1::2])[: ka.value]
+
+
+def mmc_solve(ctx, b, x, nrhs, rel_tol=1e-10, precond_handle=MMC_ZERO, prec_inner=MMC_F32, m_inner=48,
+              max_outer=400):
+    its = ctypes.c_int()
+    rel = np.zeros(int(nrhs))
+    _check(lib.mmc_solve(ctx, _ptr(b), _ptr(x), int(nrhs), float(rel_tol), int(precond_handle), int(prec_inner),
+                         int(m_inner), int(max_outer), ctypes.byref(its), rel.ctypes.data_as(_dp)), ctx)
+    return its.value, rel
+
+
+# --------------------------------------------------------------- estimators
+def mmc_trace_level(ctx, hi, lo, theta_op, deflate, n_noise, first_noise, level, prec, precond=MMC_ZERO,
+                    want_samples=True):
+    st = mmc_level_stats()
+    samples = np.zeros(2 * int(n_noise)) if want_samples else None
+    _check(lib.mmc_trace_level(ctx, int(hi), int(lo), int(theta_op), int(deflate), int(n_noise),
+                               int(first_noise), int(level), int(prec), int(precond), ctypes.byref(st),
+                               samples.ctypes.data_as(_dp) if want_samples else None), ctx)
+    s = st.as_dict()
+    if want_samples:
+        s["samples"] = samples[0::2] + 1j * samples[1::2]
+    return s
+
+
+def mmc_trace_exact(ctx, handle, theta_op, method, prec=MMC_F64):
+    out = np.zeros(2)
+    _check(lib.mmc_trace_exact(ctx, int(handle), int(theta_op), int(method), int(prec), out.ctypes.data_as(_dp)),
+           ctx)
+    return out[0] + 1j * out[1]
+
+
+def mmc_probe_colours(ctx, reach):
+    n = ctypes.c_int()
+    _check(lib.mmc_probe_colours(ctx, int(reach), ctypes.byref(n)), ctx)
+    return n.value
+
+
+# ---------------------------------------------------------- host-only helpers
+def mmc_harmonic_ritz(H):
+    H = np.asfortranarray(H, dtype=np.complex128)
+    m = H.shape[1]
+    out = np.zeros(2 * m)
+    _check(lib.mmc_harmonic_ritz(int(m), H.ctypes.data_as(_dp), int(H.shape[0]), out.ctypes.data_as(_dp)))
+    return out[0::2] + 1j * out[1::2]
+
+
+def mmc_leja_order(theta):
+    theta, p = _cplx(theta)
+    out = np.zeros(2 * theta.size)
+    _check(lib.mmc_leja_order(int(theta.size), p, out.ctypes.data_as(_dp)))
+    return out[0::2] + 1j * out[1::2]
+
+
+def mmc_eig(A, vectors=False):
+    A = np.asfortranarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    w = np.zeros(2 * n)
+    vr = np.zeros(2 * n * n) if vectors else None
+    _check(lib.mmc_eig(int(n), A.ctypes.data_as(_dp), int(n), w.ctypes.data_as(_dp),
+                       vr.ctypes.data_as(_dp) if vectors else None))
+    ev = w[0::2] + 1j * w[1::2]
+    if not vectors:
+        return ev
+    V = (vr[0::2] + 1j * vr[1::2]).reshape(n, n, order="F")
+    return ev, V
