@@ -211,6 +211,45 @@ int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec
 /* Number of colours of the probing colouring chosen for a reach (L1 distance). */
 int mmc_probe_colours(mmc_ctx* ctx, int reach, int* n_colours);
 
+/* ------------------------------------------------------------ profiling */
+
+/* Counters of the fused step kernel (the stencil / polynomial-step hot loop):
+ * launches, summed CUDA-event time of those launches, algorithmic bytes (each
+ * input, output, aux and accumulator element once, the 4 links of a site once
+ * per rhs block, the noise codes once) and flops (1368 per site and active
+ * rhs for a hop, 48 more per epilogue term), plus the number of every kernel
+ * the library launched.  Not part of the paper: bookkeeping for measurement. */
+typedef struct {
+  long long step_launches;
+  double step_ms;
+  double step_bytes;
+  double step_flops;
+  long long all_launches;
+} mmc_profile_stats;
+
+/* enable != 0 starts recording (counters reset); 0 stops.  While enabled every
+ * step launch is bracketed by CUDA events on its stream. */
+int mmc_profile(mmc_ctx* ctx, int enable);
+/* Synchronise the context's work and read the counters. */
+int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out);
+
+/* Launch variant of the fused step kernel for precision prec: rpt right-hand
+ * sides per lane (1, 2; F64 uses 1), minb = minimum resident CTAs per SM asked
+ * of the compiler (1: no register cap; 3 or 4: capped), spc = sites per CTA
+ * (16..1024, power of two).  Values <= 0 keep the current setting. */
+int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc);
+/* Autotuner: time every step-kernel variant on an nrhs-vector field of
+ * precision prec (random data, CUDA events, median of 3 after a warm-up),
+ * keep the fastest for that precision and return it (best[3] = rpt, minb, spc)
+ * with its time per launch in ms. */
+int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms);
+
+/* Replace the device links by a new host field (same layout as mmc_load_gauge)
+ * keeping kappa, polynomials and eigenpairs: for a caller that streams the same
+ * configuration, or accepts them as fixed approximations (any fixed polynomial
+ * keeps the estimator of Eq. 2 unbiased). */
+int mmc_update_gauge(mmc_ctx* ctx, const double* U);
+
 /* ---------------------------------------------------- host-only helpers */
 
 /* Harmonic Ritz values of a GMRES(m) cycle (Sec. 3) from its (m+1) x m Hessenberg

@@ -64,6 +64,10 @@ int mmc_destroy(mmc_ctx* ctx) {
   if (ctx->links32) cudaFree(ctx->links32);
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
+  if (ctx->Z32) cudaFree(ctx->Z32);
+  if (ctx->U32) cudaFree(ctx->U32);
+  prof_collect(ctx);
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return MMC_OK;
@@ -87,11 +91,15 @@ int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiod
   // canonical [mu][site][3][3] -> device [site][mu][9] (FP64) and [site][mu][10] (FP32, padded)
   std::vector<double2> h64(size_t(V) * 4 * 9);
   std::vector<float2> h32(size_t(V) * 4 * 10, make_float2(0.f, 0.f));
+  // the antiperiodic time phase is folded into U_t at t = Lt-1: both hops across the
+  // boundary (forward from t = Lt-1, backward from t = 0) use that link
+  const int slice = ctx->dims[0] * ctx->dims[1] * ctx->dims[2];
   for (int mu = 0; mu < 4; ++mu)
     for (int s = 0; s < V; ++s)
       for (int k = 0; k < 9; ++k) {
         size_t src = ((size_t(mu) * V + s) * 9 + k) * 2;
-        double re = U[src], im = U[src + 1];
+        const double ph = (t_antiperiodic && mu == 3 && s / slice == ctx->dims[3] - 1) ? -1.0 : 1.0;
+        double re = ph * U[src], im = ph * U[src + 1];
         h64[(size_t(s) * 4 + mu) * 9 + k] = make_double2(re, im);
         h32[(size_t(s) * 4 + mu) * 10 + k] = make_float2(float(re), float(im));
       }
@@ -105,6 +113,124 @@ int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiod
   ctx->polys.clear();
   ctx->k_defl = 0;
   ctx->lambda.clear();
+  return MMC_OK;
+}
+
+int mmc_update_gauge(mmc_ctx* ctx, const double* U) {
+  if (!ctx || !U) return MMC_ERR_ARG;
+  if (!ctx->gauge) RET(MMC_ERR_STATE, "mmc_update_gauge: no gauge field loaded");
+  auto polys = ctx->polys;
+  const int kd = ctx->k_defl;
+  auto lam = ctx->lambda;
+  TRY(mmc_load_gauge(ctx, U, ctx->kappa, ctx->tap));
+  ctx->polys = polys;
+  ctx->k_defl = kd;
+  ctx->lambda = lam;
+  return MMC_OK;
+}
+
+int mmc_profile(mmc_ctx* ctx, int enable) {
+  if (!ctx) return MMC_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  TRY(prof_collect(ctx));
+  if (enable) {
+    ctx->prof_launches = 0;
+    ctx->prof_ms = ctx->prof_bytes = ctx->prof_flops = 0;
+    ctx->launches0 = mmc::launch_count();
+  }
+  ctx->prof = enable != 0;
+  return MMC_OK;
+}
+
+int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out) {
+  if (!ctx || !out) return MMC_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(prof_collect(ctx));
+  out->step_launches = ctx->prof_launches;
+  out->step_ms = ctx->prof_ms;
+  out->step_bytes = ctx->prof_bytes;
+  out->step_flops = ctx->prof_flops;
+  out->all_launches = mmc::launch_count() - ctx->launches0;
+  return MMC_OK;
+}
+
+int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
+  if (!ctx || prec < 0 || prec > 2) return MMC_ERR_ARG;
+  if (rpt > 0) {
+    if (rpt != 1 && rpt != 2) RET(MMC_ERR_ARG, "rpt must be 1 or 2");
+    ctx->var_rpt[prec] = prec == MMC_F64 ? 1 : rpt;
+  }
+  if (minb > 0) ctx->var_minb[prec] = minb;
+  if (spc > 0) {
+    if (spc < 16 || spc > 1024 || (spc & (spc - 1))) RET(MMC_ERR_ARG, "spc must be a power of two in 16..1024");
+    ctx->spc_step = spc;
+  }
+  return MMC_OK;
+}
+
+int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
+  TRY(check_ctx(ctx));
+  if (nrhs < 1 || prec < 0 || prec > 2) RET(MMC_ERR_ARG, "mmc_autotune: bad argument");
+  cudaStream_t s = ctx->stream;
+  geom g = make_geom(ctx, nrhs);
+  void *x, *y;
+  TRY(scratch(ctx, "tune_x", field_bytes(g, prec), &x));
+  TRY(scratch(ctx, "tune_y", field_bytes(g, prec), &y));
+  std::vector<uint2> ids(g.npad);
+  for (int r = 0; r < g.npad; ++r) ids[r] = make_uint2(7u, uint32_t(r));
+  void* dids;
+  TRY(scratch(ctx, "ids", ids.size() * sizeof(uint2), &dids));
+  CK(cudaMemcpyAsync(dids, ids.data(), ids.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+  CK(mmc::launch_noise(prec, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, x, nullptr, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int rpts[2] = {1, 2};
+  const int minbs[3] = {1, 3, 4};
+  const int spcs[4] = {32, 64, 128, 256};
+  double best_ms = 1e300;
+  int br = ctx->var_rpt[prec], bm = ctx->var_minb[prec], bs = ctx->spc_step;
+  for (int ri = 0; ri < 2; ++ri) {
+    if (prec == MMC_F64 && rpts[ri] != 1) continue;
+    if (rpts[ri] > g.R) continue;
+    for (int mi = 0; mi < 3; ++mi) {
+      for (int si = 0; si < 4; ++si) {
+        ctx->var_rpt[prec] = rpts[ri];
+        ctx->var_minb[prec] = minbs[mi];
+        ctx->spc_step = spcs[si];
+        TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
+        std::vector<float> t;
+        for (int rep = 0; rep < 3; ++rep) {
+          CK(cudaEventRecord(e0, s));
+          TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
+          CK(cudaEventRecord(e1, s));
+          CK(cudaEventSynchronize(e1));
+          float ms;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        if (t[1] < best_ms) {
+          best_ms = t[1];
+          br = rpts[ri];
+          bm = minbs[mi];
+          bs = spcs[si];
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->var_rpt[prec] = br;
+  ctx->var_minb[prec] = bm;
+  ctx->spc_step = bs;
+  if (best) {
+    best[0] = br;
+    best[1] = bm;
+    best[2] = bs;
+  }
+  if (ms_out) *ms_out = best_ms;
   return MMC_OK;
 }
 

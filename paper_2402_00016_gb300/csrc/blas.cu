@@ -63,6 +63,34 @@ __device__ __forceinline__ double2 get<__nv_bfloat162>(const __nv_bfloat162* f, 
   return make_double2(v.x, v.y);
 }
 
+// Arithmetic precision of a field type: FP64 fields compute in FP64; FP32 and BF16
+// fields in FP32 (GB300 runs FP64 at a small fraction of the FP32 rate).
+template <typename T>
+struct Arith {
+  using R = float;
+  using C = float2;
+};
+template <>
+struct Arith<double2> {
+  using R = double;
+  using C = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ typename Arith<T>::C getc(const T* f, size_t i);
+template <>
+__device__ __forceinline__ double2 getc<double2>(const double2* f, size_t i) {
+  return f[i];
+}
+template <>
+__device__ __forceinline__ float2 getc<float2>(const float2* f, size_t i) {
+  return f[i];
+}
+template <>
+__device__ __forceinline__ float2 getc<__nv_bfloat162>(const __nv_bfloat162* f, size_t i) {
+  return __bfloat1622float2(f[i]);
+}
+
 __device__ __forceinline__ size_t fidx(const geom& g, int rb, int site, int c, int r) {
   return ((size_t(rb) * g.V + site) * 12 + c) * g.R + r;
 }
@@ -179,27 +207,32 @@ __device__ __forceinline__ void theta_dot(const double2 (&a)[12], const double2 
 template <typename T>
 __global__ void multidot_kernel(geom g, const T* A, size_t a_stride, int nvec, const T* w, int theta, int spc,
                                 double2* partial) {
+  using R = typename Arith<T>::R;
+  using C = typename Arith<T>::C;
   __shared__ double2 sh[8 * 32];
   const int rb = blockIdx.y;
   const int r = threadIdx.x % g.R;
   const int spp = blockDim.x / g.R;
   const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
   for (int i = 0; i < nvec; ++i) {
-    double re = 0, im = 0;
+    R re = 0, im = 0;
     for (int s0 = s_begin; s0 < s_end; s0 += spp) {
       int site = s0 + threadIdx.x / g.R;
       if (site >= s_end) continue;
-      double2 a[12], x[12];
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
-        a[c] = get<T>(A + size_t(i) * a_stride, fidx(g, rb, site, c, r));
-        x[c] = get<T>(w, fidx(g, rb, site, c, r));
+        const int src = (theta == 1) ? (c + 6) % 12 : c;
+        const R sg = (theta == 2 && c >= 6) ? R(-1) : R(1);
+        C a = getc<T>(A + size_t(i) * a_stride, fidx(g, rb, site, c, r));
+        C x = getc<T>(w, fidx(g, rb, site, src, r));
+        re += sg * (a.x * x.x + a.y * x.y);
+        im += sg * (a.x * x.y - a.y * x.x);
       }
-      theta_dot(a, x, theta, re, im);
     }
-    cta_reduce_r(re, im, g.R, sh);
+    double dre = re, dim = im;
+    cta_reduce_r(dre, dim, g.R, sh);
     if (threadIdx.x < g.R)
-      partial[(size_t(blockIdx.x) * nvec + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(re, im);
+      partial[(size_t(blockIdx.x) * nvec + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(dre, dim);
   }
 }
 
@@ -221,23 +254,28 @@ __global__ void reduce_kernel(const double2* partial, int nbx, int nvec, int npa
 
 template <typename T>
 __global__ void basis_update_kernel(geom g, const T* A, size_t a_stride, int nvec, const double2* h, T* w) {
+  using R = typename Arith<T>::R;
+  using C = typename Arith<T>::C;
   const int rb = blockIdx.y;
   const int r = threadIdx.x % g.R;
   const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
   if (site >= g.V) return;
   const int rg = rb * g.R + r;
-#pragma unroll 1
-  for (int c = 0; c < 12; ++c) {
-    size_t e = fidx(g, rb, site, c, r);
-    double2 acc = get<T>(w, e);
-    for (int i = 0; i < nvec; ++i) {
-      double2 a = get<T>(A + size_t(i) * a_stride, e);
-      double2 hh = h[size_t(i) * g.npad + rg];
-      acc.x -= a.x * hh.x - a.y * hh.y;
-      acc.y -= a.x * hh.y + a.y * hh.x;
+  C acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = getc<T>(w, fidx(g, rb, site, c, r));
+  for (int i = 0; i < nvec; ++i) {
+    const double2 hd = h[size_t(i) * g.npad + rg];
+    const R hx = R(hd.x), hy = R(hd.y);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      C a = getc<T>(A + size_t(i) * a_stride, fidx(g, rb, site, c, r));
+      acc[c].x -= a.x * hx - a.y * hy;
+      acc[c].y -= a.x * hy + a.y * hx;
     }
-    put<T>(w, e, acc.x, acc.y);
   }
+#pragma unroll
+  for (int c = 0; c < 12; ++c) put<T>(w, fidx(g, rb, site, c, r), acc[c].x, acc[c].y);
 }
 
 template <typename T>
@@ -323,9 +361,12 @@ __global__ void bilinear_codes_kernel(geom g, const uint32_t* codes, int theta, 
 }
 
 // a[i][r] = sum conj(eta_r) Theta z_i ; b[i][r] = sum conj(u_i) eta_r.  z_i, u_i are
-// single-vector FP64 fields ([site][12], R = 1 layout).
-__global__ void defl_proj_kernel(geom g, const uint32_t* codes, int theta, const double2* Z, const double2* U,
-                                 int k, int spc, double2* pa, double2* pb) {
+// single-vector fields ([site][12], R = 1 layout) of type E (double2 or float2);
+// the per-thread sums run in E's precision, the CTA reduction in FP64.
+template <typename E>
+__global__ void defl_proj_kernel(geom g, const uint32_t* codes, int theta, const E* Z, const E* U, int k, int spc,
+                                 double2* pa, double2* pb) {
+  using R = decltype(E().x);
   __shared__ double2 sh[8 * 32];
   const int rb = blockIdx.y;
   const int r = threadIdx.x % g.R;
@@ -333,30 +374,34 @@ __global__ void defl_proj_kernel(geom g, const uint32_t* codes, int theta, const
   const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
   const size_t n = size_t(g.V) * 12;
   for (int i = 0; i < k; ++i) {
-    double are = 0, aim = 0, bre = 0, bim = 0;
+    R are = 0, aim = 0, bre = 0, bim = 0;
     for (int s0 = s_begin; s0 < s_end; s0 += spp) {
       int site = s0 + threadIdx.x / g.R;
       if (site >= s_end) continue;
       uint32_t code = codes[(size_t(rb) * g.V + site) * g.R + r];
-      double2 eta[12], z[12];
+      const E* zp = Z + size_t(i) * n + size_t(site) * 12;
+      const E* up = U + size_t(i) * n + size_t(site) * 12;
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
-        uint32_t kk = (code >> (2 * c)) & 3u;
-        eta[c] = make_double2(kk == 0 ? 1.0 : (kk == 2 ? -1.0 : 0.0), kk == 1 ? 1.0 : (kk == 3 ? -1.0 : 0.0));
-        z[c] = Z[size_t(i) * n + size_t(site) * 12 + c];
-      }
-      theta_dot(eta, z, theta, are, aim);
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        double2 u = U[size_t(i) * n + size_t(site) * 12 + c];
-        bre += u.x * eta[c].x + u.y * eta[c].y;
-        bim += u.x * eta[c].y - u.y * eta[c].x;
+        // a: conj(eta_c) (Theta z)_c ; b: conj(u_c) eta_c with eta_c = i^k
+        const int src = (theta == 1) ? (c + 6) % 12 : c;
+        const R sg = (theta == 2 && c >= 6) ? R(-1) : R(1);
+        E zv = zp[src];
+        E uv = up[c];
+        const uint32_t kk = (code >> (2 * c)) & 3u;
+        R er = (kk == 0) ? R(1) : (kk == 2 ? R(-1) : R(0));
+        R ei = (kk == 1) ? R(1) : (kk == 3 ? R(-1) : R(0));
+        are += sg * (er * zv.x + ei * zv.y);
+        aim += sg * (er * zv.y - ei * zv.x);
+        bre += uv.x * er + uv.y * ei;
+        bim += uv.x * ei - uv.y * er;
       }
     }
-    cta_reduce_r(are, aim, g.R, sh);
-    if (threadIdx.x < g.R) pa[(size_t(blockIdx.x) * k + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(are, aim);
-    cta_reduce_r(bre, bim, g.R, sh);
-    if (threadIdx.x < g.R) pb[(size_t(blockIdx.x) * k + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(bre, bim);
+    double dar = are, dai = aim, dbr = bre, dbi = bim;
+    cta_reduce_r(dar, dai, g.R, sh);
+    if (threadIdx.x < g.R) pa[(size_t(blockIdx.x) * k + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(dar, dai);
+    cta_reduce_r(dbr, dbi, g.R, sh);
+    if (threadIdx.x < g.R) pb[(size_t(blockIdx.x) * k + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(dbr, dbi);
   }
 }
 
@@ -440,6 +485,7 @@ cudaError_t launch_noise(int prec, geom g, const uint2* ids, uint32_t tag, uint6
     noise_kernel<float2><<<grid, th, 0, s>>>(g, ids, tag, k0, k1, (float2*)field, codes);
   else
     noise_kernel<__nv_bfloat162><<<grid, th, 0, s>>>(g, ids, tag, k0, k1, (__nv_bfloat162*)field, codes);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -453,6 +499,7 @@ cudaError_t launch_probe(int prec, geom g, const int* site_colour, const int2* p
     probe_kernel<float2><<<grid, th, 0, s>>>(g, site_colour, probe, (float2*)field);
   else
     probe_kernel<__nv_bfloat162><<<grid, th, 0, s>>>(g, site_colour, probe, (__nv_bfloat162*)field);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -465,6 +512,7 @@ cudaError_t launch_pack(int prec, geom g, int nrhs, const double2* canon, void* 
     pack_kernel<float2><<<grid, th, 0, s>>>(g, nrhs, canon, (float2*)field);
   else
     pack_kernel<__nv_bfloat162><<<grid, th, 0, s>>>(g, nrhs, canon, (__nv_bfloat162*)field);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -477,6 +525,7 @@ cudaError_t launch_unpack(int prec, geom g, int nrhs, const void* field, double2
     unpack_kernel<float2><<<grid, th, 0, s>>>(g, nrhs, (const float2*)field, canon);
   else
     unpack_kernel<__nv_bfloat162><<<grid, th, 0, s>>>(g, nrhs, (const __nv_bfloat162*)field, canon);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -499,6 +548,7 @@ cudaError_t launch_convert(int pd, void* dst, int ps, const void* src, geom g, c
     convert_from<float2>(ps, n, (float2*)dst, src, s);
   else
     convert_from<__nv_bfloat162>(ps, n, (__nv_bfloat162*)dst, src, s);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -511,6 +561,7 @@ cudaError_t launch_multidot(int prec, geom g, const void* A, size_t a_stride, in
   else
     multidot_kernel<float2><<<grid, 256, 0, s>>>(g, (const float2*)A, a_stride, nvec, (const float2*)w, theta, spc,
                                                  partial);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -518,6 +569,7 @@ cudaError_t launch_reduce(const double2* partial, int nbx, int nvec, int npad, d
                           cudaStream_t s) {
   int n = nvec * npad;
   reduce_kernel<<<(n + 127) / 128, 128, 0, s>>>(partial, nbx, nvec, npad, out, accumulate);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -528,6 +580,7 @@ cudaError_t launch_basis_update(int prec, geom g, const void* A, size_t a_stride
     basis_update_kernel<double2><<<grid, 256, 0, s>>>(g, (const double2*)A, a_stride, nvec, h, (double2*)w);
   else
     basis_update_kernel<float2><<<grid, 256, 0, s>>>(g, (const float2*)A, a_stride, nvec, h, (float2*)w);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -537,6 +590,7 @@ cudaError_t launch_normalise(int prec, geom g, const void* src, const double2* n
     normalise_kernel<double2><<<grid, 256, 0, s>>>(g, (const double2*)src, nrm2, (double2*)dst);
   else
     normalise_kernel<float2><<<grid, 256, 0, s>>>(g, (const float2*)src, nrm2, (float2*)dst);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -549,6 +603,7 @@ cudaError_t launch_axpby(int prec, geom g, const double2* a, const void* x, cons
     axpby_kernel<float2><<<grid, 256, 0, s>>>(g, a, (const float2*)x, b, (float2*)y);
   else
     axpby_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>(g, a, (const __nv_bfloat162*)x, b, (__nv_bfloat162*)y);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -560,6 +615,7 @@ cudaError_t launch_gamma(int prec, geom g, int theta, const void* src, void* dst
     gamma_kernel<float2><<<grid, 256, 0, s>>>(g, theta, (const float2*)src, (float2*)dst);
   else
     gamma_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>(g, theta, (const __nv_bfloat162*)src, (__nv_bfloat162*)dst);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -573,13 +629,20 @@ cudaError_t launch_bilinear_codes(int prec, geom g, const uint32_t* codes, int t
   else
     bilinear_codes_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>(g, codes, theta, (const __nv_bfloat162*)x, spc,
                                                                partial);
+  count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_defl_proj(geom g, const uint32_t* codes, int theta, const double2* Z, const double2* U, int k,
+cudaError_t launch_defl_proj(int prec, geom g, const uint32_t* codes, int theta, const void* Z, const void* U, int k,
                              int spc, double2* pa, double2* pb, cudaStream_t s) {
   dim3 grid((g.V + spc - 1) / spc, g.nrb);
-  defl_proj_kernel<<<grid, 256, 0, s>>>(g, codes, theta, Z, U, k, spc, pa, pb);
+  if (prec == 0)
+    defl_proj_kernel<double2><<<grid, 256, 0, s>>>(g, codes, theta, (const double2*)Z, (const double2*)U, k, spc, pa,
+                                                   pb);
+  else
+    defl_proj_kernel<float2><<<grid, 256, 0, s>>>(g, codes, theta, (const float2*)Z, (const float2*)U, k, spc, pa,
+                                                  pb);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -590,6 +653,7 @@ cudaError_t launch_vec_proj(int prec, geom g, const double2* Vv, int k, const vo
     vec_proj_kernel<double2><<<grid, 256, 0, s>>>(g, Vv, k, (const double2*)f, spc, partial);
   else
     vec_proj_kernel<float2><<<grid, 256, 0, s>>>(g, Vv, k, (const float2*)f, spc, partial);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -600,11 +664,13 @@ cudaError_t launch_vec_update(int prec, geom g, const double2* Vv, int k, const 
     vec_update_kernel<double2><<<grid, 256, 0, s>>>(g, Vv, k, coef, (double2*)f);
   else
     vec_update_kernel<float2><<<grid, 256, 0, s>>>(g, Vv, k, coef, (float2*)f);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_add2(const double2* a, const double2* b, double2* out, int n, cudaStream_t s) {
   add2_kernel<<<(n + 127) / 128, 128, 0, s>>>(a, b, out, n);
+  count_launch();
   return cudaGetLastError();
 }
 

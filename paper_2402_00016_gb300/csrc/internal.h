@@ -51,10 +51,21 @@ struct mmc_ctx {
   std::vector<mmc::cd> lambda;
   double2* Z = nullptr;
   double2* U = nullptr;
+  float2* Z32 = nullptr;  // FP32 copies used by the FP32 / BF16 levels (projections and correction alike)
+  float2* U32 = nullptr;
   std::map<std::string, mmc::host::DevBuf> scratch;
   std::string err;
   long long matvecs = 0;
-  int spc_step = 64;  // sites per CTA of the step kernel
+  int spc_step = 64;  // sites per CTA of the step kernel (all precisions: partial buffers depend on it)
+  int var_rpt[3] = {1, 2, 2};
+  int var_minb[3] = {1, 1, 1};
+  // profiling (mmc_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  long long prof_launches = 0;
+  double prof_ms = 0, prof_bytes = 0, prof_flops = 0;
+  long long launches0 = 0;
 };
 
 namespace mmc {
@@ -122,10 +133,9 @@ inline int scratch(mmc_ctx* ctx, const std::string& key, size_t bytes, void** ou
   return MMC_OK;
 }
 
-inline int rpt_for(int prec, int R) {
+inline int rpt_for(const mmc_ctx* ctx, int prec, int R) {
   if (prec == MMC_F64) return 1;
-  if (prec == MMC_F32) return R >= 2 ? 2 : 1;
-  return R >= 2 ? 2 : 1;
+  return std::min(ctx->var_rpt[prec], R);
 }
 
 inline int log2i(int v) {
@@ -159,6 +169,31 @@ struct Run {
 
 inline int nbx_for(const mmc_ctx* ctx, int spc) { return (ctx->V + spc - 1) / spc; }
 
+inline int prof_event(mmc_ctx* ctx, cudaEvent_t* e) {
+  if (ctx->ev_pool.empty()) {
+    cudaEvent_t ev;
+    CK(cudaEventCreate(&ev));
+    ctx->ev_pool.push_back(ev);
+  }
+  *e = ctx->ev_pool.back();
+  ctx->ev_pool.pop_back();
+  return MMC_OK;
+}
+
+// Collect the elapsed times of finished event pairs (synchronises on each pair).
+inline int prof_collect(mmc_ctx* ctx) {
+  for (auto& pr : ctx->ev_pending) {
+    CK(cudaEventSynchronize(pr.second));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    ctx->prof_ms += ms;
+    ctx->ev_pool.push_back(pr.first);
+    ctx->ev_pool.push_back(pr.second);
+  }
+  ctx->ev_pending.clear();
+  return MMC_OK;
+}
+
 inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
   if (run.steps.empty()) return MMC_OK;
   const geom& g = run.g;
@@ -170,7 +205,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
   void* dcoef;
   TRY(scratch(ctx, "coef", host.size() * sizeof(double2), &dcoef));
   CK(cudaMemcpyAsync(dcoef, host.data(), host.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-  const int rpt = rpt_for(run.prec, g.R);
+  const int rpt = rpt_for(ctx, run.prec, g.R);
   for (size_t k = 0; k < run.steps.size(); ++k) {
     const Step& st = run.steps[k];
     mmc::step_params p;
@@ -198,7 +233,30 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     p.tap = ctx->tap;
     p.theta = run.theta;
     p.flags = st.flags | (run.dagger ? mmc::SF_DAGGER : 0);
-    CK(mmc::launch_step(run.prec, rpt, p, g.nrb, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->prof) {
+      TRY(prof_event(ctx, &e0));
+      TRY(prof_event(ctx, &e1));
+      CK(cudaEventRecord(e0, s));
+    }
+    CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec], p, g.nrb, s));
+    if (ctx->prof) {
+      CK(cudaEventRecord(e1, s));
+      ctx->ev_pending.push_back({e0, e1});
+      if (ctx->ev_pending.size() > 4096) TRY(prof_collect(ctx));
+      ctx->prof_launches += 1;
+      // algorithmic bytes and flops of this launch (all rhs blocks active)
+      const double sb = double(elem_bytes(run.prec)) * 12;  // one spinor, one rhs
+      const double per_rhs = sb * ((st.flags & mmc::SF_HOP) ? 2 : 1) * ((st.flags & mmc::SF_WRITE) ? 1 : 0) +
+                             (((st.flags & mmc::SF_WRITE) == 0) ? sb : 0.0) +
+                             ((st.flags & mmc::SF_AUX) ? sb : 0.0) +
+                             ((st.flags & mmc::SF_YACC) ? 2.0 * 12 * (run.prec == MMC_F64 ? 16 : 8) : 0.0) +
+                             ((st.flags & mmc::SF_BIL_CODES) ? 4.0 : 0.0) +
+                             ((st.flags & mmc::SF_BIL_LEFT) ? sb : 0.0);
+      const double links = (st.flags & mmc::SF_HOP) ? 4.0 * 9 * (run.prec == MMC_F64 ? 16 : 8) : 0.0;
+      ctx->prof_bytes += double(ctx->V) * (double(g.npad) * per_rhs + double(g.nrb) * links);
+      ctx->prof_flops += double(ctx->V) * g.npad * (((st.flags & mmc::SF_HOP) ? 1368.0 : 0.0) + 48.0);
+    }
     if (st.flags & mmc::SF_HOP) ctx->matvecs += g.npad;
   }
   return MMC_OK;

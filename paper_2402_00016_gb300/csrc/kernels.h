@@ -12,8 +12,13 @@ struct geom {
   int V, R, nrb, npad;
 };
 
-// Fused stencil step (stencil.cu).  prec: 0 F64, 1 F32, 2 BF16; rpt: rhs per lane.
-cudaError_t launch_step(int prec, int rpt, const step_params& p, int n_rb, cudaStream_t s);
+// Number of kernels the library has launched in this process (every launch_* call).
+long long launch_count();
+void count_launch(int n = 1);
+
+// Fused stencil step (stencil.cu).  prec: 0 F64, 1 F32, 2 BF16; rpt: rhs per lane;
+// minb: minimum resident CTAs per SM asked of the compiler (caps registers).
+cudaError_t launch_step(int prec, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s);
 
 // Z(4) noise (Sec. 1) into a field of precision prec and/or packed codes.
 // ids[r] = (level, noise index) for rhs r (npad entries, device); entries with
@@ -55,9 +60,10 @@ cudaError_t launch_gamma(int prec, geom g, int theta, const void* src, void* dst
 cudaError_t launch_bilinear_codes(int prec, geom g, const uint32_t* codes, int theta, const void* x, int spc,
                                   double2* partial, cudaStream_t s);
 
-// Deflation projections (Sec. 7) of noise codes against k FP64 single-vector fields:
-// a[i][r] = sum conj(eta_r) (Theta z_i),  b[i][r] = sum conj(u_i) eta_r  (partials per CTA).
-cudaError_t launch_defl_proj(geom g, const uint32_t* codes, int theta, const double2* Z, const double2* U,
+// Deflation projections (Sec. 7) of noise codes against k single-vector fields (prec 0:
+// FP64 double2, 1: FP32 float2): a[i][r] = sum conj(eta_r) (Theta z_i),
+// b[i][r] = sum conj(u_i) eta_r  (partials per CTA).
+cudaError_t launch_defl_proj(int prec, geom g, const uint32_t* codes, int theta, const void* Z, const void* U,
                              int k, int spc, double2* partial_a, double2* partial_b, cudaStream_t s);
 
 // Projections of a batch field on k single-vector FP64 fields v_i and the matching

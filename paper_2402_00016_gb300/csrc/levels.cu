@@ -231,7 +231,10 @@ Colouring find_colouring(const int* L, int V, int reach) {
     }
   }
   std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.n < b.n; });
-  const long long lower = (long long)D.size() / 8;  // cheap lower bound: skip hopeless tiny counts
+  // lower bound: the points of an L1 ball of radius reach/2 need distinct colours
+  long long lower = 1;
+  for (auto& d : D)
+    if (std::abs(d[0]) + std::abs(d[1]) + std::abs(d[2]) + std::abs(d[3]) <= reach / 2) ++lower;
   std::mt19937 rng(12345);
   for (const Cand& c : cands) {
     if (c.n >= V || c.n < lower) continue;
@@ -378,7 +381,10 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
   const int kk = int(keep.size());
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
+  if (ctx->Z32) cudaFree(ctx->Z32);
+  if (ctx->U32) cudaFree(ctx->U32);
   ctx->Z = ctx->U = nullptr;
+  ctx->Z32 = ctx->U32 = nullptr;
   ctx->k_defl = 0;
   ctx->lambda.clear();
   if (kk > 0) {
@@ -416,6 +422,11 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
       CK(cudaMemsetAsync(ui, 0, fb, s));
       CK(mmc::launch_basis_update(MMC_F64, g, W, n, kk, (const double2*)dh, ui, s));
     }
+    CK(cudaMalloc(&ctx->Z32, fb / 2 * kk));
+    CK(cudaMalloc(&ctx->U32, fb / 2 * kk));
+    const geom gk = {ctx->V * kk, 1, 1, 1};  // kk single vectors as one flat field
+    CK(mmc::launch_convert(MMC_F32, ctx->Z32, MMC_F64, ctx->Z, gk, s));
+    CK(mmc::launch_convert(MMC_F32, ctx->U32, MMC_F64, ctx->U, gk, s));
     CK(cudaStreamSynchronize(s));
     for (int i = 0; i < kk; ++i) ctx->lambda.push_back(lam[keep[i]]);
     ctx->k_defl = kk;
@@ -510,8 +521,10 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     void *pa, *pb;
     TRY(scratch(ctx, "lv_pa", size_t(nb2) * k * g.npad * sizeof(double2), &pa));
     TRY(scratch(ctx, "lv_pb", size_t(nb2) * k * g.npad * sizeof(double2), &pb));
-    CK(mmc::launch_defl_proj(g, (const uint32_t*)codes, theta_op, ctx->Z, ctx->U, k, kSpc, (double2*)pa, (double2*)pb,
-                             s));
+    const int dp = prec == MMC_F64 ? MMC_F64 : MMC_F32;  // eigenvector copy matching the level's precision
+    const void* Zd = dp == MMC_F64 ? (const void*)ctx->Z : (const void*)ctx->Z32;
+    const void* Ud = dp == MMC_F64 ? (const void*)ctx->U : (const void*)ctx->U32;
+    CK(mmc::launch_defl_proj(dp, g, (const uint32_t*)codes, theta_op, Zd, Ud, k, kSpc, (double2*)pa, (double2*)pb, s));
     std::vector<cd> A, B;
     TRY(reduce_to_host(ctx, (double2*)pa, nb2, k, g.npad, A, s));
     TRY(reduce_to_host(ctx, (double2*)pb, nb2, k, g.npad, B, s));
@@ -519,8 +532,9 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     for (int i = 0; i < k; ++i) {
       cd c = poly_value(ctx, hi, ctx->lambda[i]) - (lo == MMC_ZERO ? cd(0, 0) : poly_value(ctx, lo, ctx->lambda[i]));
       for (int r = 0; r < n_noise; ++r) x[r] -= c * A[size_t(i) * g.npad + r] * B[size_t(i) * g.npad + r];
-      CK(mmc::launch_multidot(MMC_F64, g1, ctx->U + size_t(i) * n, 0, 1, ctx->Z + size_t(i) * n, theta_op, kSpc,
-                              (double2*)part, s));
+      const void* ui = dp == MMC_F64 ? (const void*)(ctx->U + size_t(i) * n) : (const void*)(ctx->U32 + size_t(i) * n);
+      const void* zi = dp == MMC_F64 ? (const void*)(ctx->Z + size_t(i) * n) : (const void*)(ctx->Z32 + size_t(i) * n);
+      CK(mmc::launch_multidot(dp, g1, ui, 0, 1, zi, theta_op, kSpc, (double2*)part, s));
       std::vector<cd> d;
       TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, 1, d, s));
       corr += c * d[0];

@@ -26,6 +26,25 @@ namespace mmc {
 namespace {
 
 // ------------------------------------------------------------ load / store
+// Read-only loads as volatile PTX: they stay in program order with respect to the
+// per-hop compiler barriers, which bounds the loads in flight per thread to one
+// neighbour (and the register footprint with it).
+__device__ __forceinline__ uint4 ldv4(const void* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ uint2 ldv2(const void* p) {
+  uint2 r;
+  asm volatile("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ uint32_t ldv1(const void* p) {
+  uint32_t r;
+  asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(r) : "l"(p));
+  return r;
+}
+
 template <typename S>
 struct StoreTraits;
 
@@ -52,24 +71,24 @@ __device__ __forceinline__ cx<float> to_cx(__nv_bfloat162 v) {
 template <typename S, int RPT>
 __device__ __forceinline__ void load_rpt(const S* p, cx<typename StoreTraits<S>::R> (&v)[RPT]) {
   if constexpr (sizeof(S) * RPT == 16) {
-    uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+    uint4 raw = ldv4(p);
     const S* s = reinterpret_cast<const S*>(&raw);
 #pragma unroll
     for (int j = 0; j < RPT; ++j) v[j] = to_cx(s[j]);
   } else if constexpr (sizeof(S) * RPT == 8) {
-    uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+    uint2 raw = ldv2(p);
     const S* s = reinterpret_cast<const S*>(&raw);
 #pragma unroll
     for (int j = 0; j < RPT; ++j) v[j] = to_cx(s[j]);
   } else if constexpr (sizeof(S) * RPT == 4) {
-    uint32_t raw = __ldg(reinterpret_cast<const unsigned int*>(p));
+    uint32_t raw = ldv1(p);
     const S* s = reinterpret_cast<const S*>(&raw);
 #pragma unroll
     for (int j = 0; j < RPT; ++j) v[j] = to_cx(s[j]);
   } else {
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
-      uint4 raw = __ldg(reinterpret_cast<const uint4*>(p + j));
+      uint4 raw = ldv4(p + j);
       v[j] = to_cx(*reinterpret_cast<const S*>(&raw));
     }
   }
@@ -142,7 +161,8 @@ __device__ __forceinline__ void load_link(const void* links, int site, int mu, L
   const double2* p = reinterpret_cast<const double2*>(links) + (size_t(site) * 4 + mu) * 9;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    double2 v = __ldg(p + k);
+    uint4 raw = ldv4(p + k);
+    double2 v = *reinterpret_cast<const double2*>(&raw);
     L.u[k] = cmake(v.x, v.y);
   }
 }
@@ -150,22 +170,23 @@ __device__ __forceinline__ void load_link(const void* links, int site, int mu, L
   const float4* p = reinterpret_cast<const float4*>(links) + (size_t(site) * 4 + mu) * 5;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    float4 v = __ldg(p + k);
+    uint4 raw = ldv4(p + k);
+    float4 v = *reinterpret_cast<const float4*>(&raw);
     L.u[2 * k] = cmake(v.x, v.y);
     L.u[2 * k + 1] = cmake(v.z, v.w);
   }
-  float4 v = __ldg(p + 4);
+  uint4 raw = ldv4(p + 4);
+  float4 v = *reinterpret_cast<const float4*>(&raw);
   L.u[8] = cmake(v.x, v.y);
 }
 
 // ------------------------------------------------- one hop direction
 // Adds sgn * (1 - sg gamma_MU) W h(nbr) to acc, W = U (FWD) or U^+ (backward),
 // for RPT right-hand sides.  sg = +1 forward / -1 backward for M; flipped for M^+.
-template <typename S, int RPT, int MU>
+template <typename S, int RPT, int MU, bool DAGU, int SG>
 __device__ __forceinline__ void hop_dir(const S* nb, int R, const Link<typename StoreTraits<S>::R>& L,
-                                        bool dagU, typename StoreTraits<S>::R sg,
-                                        typename StoreTraits<S>::R bsign,
                                         cx<typename StoreTraits<S>::R> (&acc)[12][RPT]) {
+  const typename StoreTraits<S>::R sg = SG;
   using T = typename StoreTraits<S>::R;
   cx<T> h0[3][RPT], h1[3][RPT];
 #pragma unroll
@@ -199,7 +220,7 @@ __device__ __forceinline__ void hop_dir(const S* nb, int R, const Link<typename 
       cx<T> v0 = cmake(T(0), T(0)), v1 = cmake(T(0), T(0));
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        if (dagU) {
+        if (DAGU) {
           v0 = cfmac(L.u[b * 3 + a], h0[b][j], v0);
           v1 = cfmac(L.u[b * 3 + a], h1[b][j], v1);
         } else {
@@ -207,8 +228,6 @@ __device__ __forceinline__ void hop_dir(const S* nb, int R, const Link<typename 
           v1 = cfma(L.u[a * 3 + b], h1[b][j], v1);
         }
       }
-      v0 = cscale(v0, bsign);
-      v1 = cscale(v1, bsign);
       // lower half r = -sg A^+ v
       cx<T> r2, r3;
       if (MU == 0) {  // A^+ v = (i v1, i v0)
@@ -232,61 +251,44 @@ __device__ __forceinline__ void hop_dir(const S* nb, int R, const Link<typename 
   }
 }
 
-template <typename S, int RPT, int MU>
-__device__ __forceinline__ void hop_mu(const step_params& p, const S* base, int site, int coord,
-                                       int stride, int extent, int sgn_dag,
-                                       cx<typename StoreTraits<S>::R> (&acc)[12][RPT]) {
+// Compiler fence on the hop accumulators: the empty volatile asm reads and writes
+// every accumulator, so the arithmetic of one hop finishes before the (volatile)
+// loads of the next hop are issued.  This bounds the live registers to one hop.
+__device__ __forceinline__ void fence_acc(float& a, float& b, float& c, float& d) {
+  asm volatile("" : "+f"(a), "+f"(b), "+f"(c), "+f"(d));
+}
+__device__ __forceinline__ void fence_acc(double& a, double& b, double& c, double& d) {
+  asm volatile("" : "+d"(a), "+d"(b), "+d"(c), "+d"(d));
+}
+template <typename T, int RPT>
+__device__ __forceinline__ void fence(cx<T> (&acc)[12][RPT]) {
+#pragma unroll
+  for (int c = 0; c < 12; c += 2)
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) fence_acc(acc[c][j].re, acc[c][j].im, acc[c + 1][j].re, acc[c + 1][j].im);
+}
+
+// Both hops of direction MU.  The antiperiodic time phase is folded into the stored
+// links (U_t at t = Lt-1 carries the factor -1), so every hop across the boundary
+// gets it from the link itself.  KD = +1 for M, -1 for M^+ (projector signs flipped).
+template <typename S, int RPT, int MU, int KD>
+__device__ __forceinline__ void hop_mu(const step_params& p, const S* base, int site, int coord, int stride,
+                                       int extent, cx<typename StoreTraits<S>::R> (&acc)[12][RPT]) {
   using T = typename StoreTraits<S>::R;
   Link<T> L;
-  // forward neighbour x + mu
-  int fwd = (coord == extent - 1) ? site - (extent - 1) * stride : site + stride;
-  T bf = (MU == 3 && p.tap && coord == extent - 1) ? T(-1) : T(1);
+  const int fwd = (coord == extent - 1) ? site - (extent - 1) * stride : site + stride;
   load_link(p.links, site, MU, L);
-  hop_dir<S, RPT, MU>(base + size_t(fwd) * 12 * p.R, p.R, L, false, T(sgn_dag), bf, acc);
-  // backward neighbour x - mu
-  int bwd = (coord == 0) ? site + (extent - 1) * stride : site - stride;
-  T bb = (MU == 3 && p.tap && coord == 0) ? T(-1) : T(1);
+  hop_dir<S, RPT, MU, false, KD>(base + size_t(fwd) * 12 * p.R, p.R, L, acc);
+  // one neighbour's loads in flight per thread: occupancy, not hoisting, hides latency
+  fence<T, RPT>(acc);
+  const int bwd = (coord == 0) ? site + (extent - 1) * stride : site - stride;
   load_link(p.links, bwd, MU, L);
-  hop_dir<S, RPT, MU>(base + size_t(bwd) * 12 * p.R, p.R, L, true, T(-sgn_dag), bb, acc);
+  hop_dir<S, RPT, MU, true, -KD>(base + size_t(bwd) * 12 * p.R, p.R, L, acc);
+  fence<T, RPT>(acc);
 }
 
-// conj(eta_c) * (Theta psi)_c summed over the 12 components, eta = i^code.
-template <typename T>
-__device__ __forceinline__ cx<T> bil_codes(uint32_t code, int theta, const cx<T> (&v)[12]) {
-  cx<T> s = cmake(T(0), T(0));
-#pragma unroll
-  for (int c = 0; c < 12; ++c) {
-    int src = c;
-    T sgn = T(1);
-    if (theta == 1) src = (c + 6) % 12;                   // gamma_4 swaps upper and lower spins
-    if (theta == 2 && c >= 6) sgn = T(-1);                // gamma_5 = diag(1,1,-1,-1)
-    cx<T> w = v[src];
-    uint32_t k = (code >> (2 * c)) & 3u;                  // conj(i^k) * w
-    cx<T> t;
-    if (k == 0) t = w;
-    else if (k == 1) t = cmake(w.im, -w.re);
-    else if (k == 2) t = cmake(-w.re, -w.im);
-    else t = cmake(-w.im, w.re);
-    s.re += sgn * t.re;
-    s.im += sgn * t.im;
-  }
-  return s;
-}
-
-template <typename T>
-__device__ __forceinline__ cx<T> bil_left(const cx<T> (&l)[12], int theta, const cx<T> (&v)[12]) {
-  cx<T> s = cmake(T(0), T(0));
-#pragma unroll
-  for (int c = 0; c < 12; ++c) {
-    int src = (theta == 1) ? (c + 6) % 12 : c;
-    T sgn = (theta == 2 && c >= 6) ? T(-1) : T(1);
-    s = cfmac(l[c], cscale(v[src], sgn), s);
-  }
-  return s;
-}
-
-template <typename S, int RPT>
-__global__ void __launch_bounds__(128) step_kernel(step_params p) {
+template <typename S, int RPT, int KD, int MINB>
+__global__ void __launch_bounds__(128, MINB) step_kernel(step_params p) {
   using T = typename StoreTraits<S>::R;
   using Y = typename std::conditional<std::is_same<T, double>::value, double2, float2>::type;
   const int rb = blockIdx.y;
@@ -298,7 +300,6 @@ __global__ void __launch_bounds__(128) step_kernel(step_params p) {
   const int rglob = rb * p.R + r0;
   const S* in = reinterpret_cast<const S*>(p.in) + size_t(rb) * p.V * 12 * p.R;
   const int flags = p.flags;
-  const T kd = (flags & SF_DAGGER) ? T(-1) : T(1);
 
   cx<T> ca[RPT], cb[RPT], cg[RPT], cwi[RPT], cwo[RPT];
 #pragma unroll
@@ -333,89 +334,76 @@ __global__ void __launch_bounds__(128) step_kernel(step_params p) {
       int z = rest % p.Lz;
       int t = rest / p.Lz;
       const int sx = 1, sy = p.Lx, sz = p.Lx * p.Ly, st = p.Lx * p.Ly * p.Lz;
-      hop_mu<S, RPT, 0>(p, base, site, x, sx, p.Lx, int(kd), acc);
-      hop_mu<S, RPT, 1>(p, base, site, y, sy, p.Ly, int(kd), acc);
-      hop_mu<S, RPT, 2>(p, base, site, z, sz, p.Lz, int(kd), acc);
-      hop_mu<S, RPT, 3>(p, base, site, t, st, p.Lt, int(kd), acc);
+      hop_mu<S, RPT, 0, KD>(p, base, site, x, sx, p.Lx, acc);
+      hop_mu<S, RPT, 1, KD>(p, base, site, y, sy, p.Ly, acc);
+      hop_mu<S, RPT, 2, KD>(p, base, site, z, sz, p.Lz, acc);
+      hop_mu<S, RPT, 3, KD>(p, base, site, t, st, p.Lt, acc);
     }
     const size_t off = (size_t(site) * 12) * p.R + r0;  // within rhs block
     const size_t boff = size_t(rb) * p.V * 12 * p.R + off;
-    cx<T> vin[12][RPT];
+    const bool bil = (flags & (SF_BIL_CODES | SF_BIL_LEFT)) != 0;
+    uint32_t code[RPT];
+    if (flags & SF_BIL_CODES) {
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) code[j] = __ldg(p.codes + (size_t(rb) * p.V + site) * p.R + r0 + j);
+    }
+    // epilogue streamed one spin-colour component at a time: out_c = a in_c + b (D in)_c + g aux_c
+    cx<T> si[RPT], so[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) si[j] = so[j] = cmake(T(0), T(0));
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
-      cx<T> tmp[RPT];
-      load_rpt<S, RPT>(in + off + size_t(c) * p.R, tmp);
+      cx<T> vin[RPT], vout[RPT];
+      load_rpt<S, RPT>(in + off + size_t(c) * p.R, vin);
 #pragma unroll
-      for (int j = 0; j < RPT; ++j) vin[c][j] = tmp[j];
-    }
-    cx<T> vout[12][RPT];
+      for (int j = 0; j < RPT; ++j) vout[j] = cfma(cb[j], acc[c][j], cmul(ca[j], vin[j]));
+      if (flags & SF_AUX) {
+        cx<T> ax[RPT];
+        load_rpt<S, RPT>(reinterpret_cast<const S*>(p.aux) + boff + size_t(c) * p.R, ax);
 #pragma unroll
-    for (int c = 0; c < 12; ++c)
-#pragma unroll
-      for (int j = 0; j < RPT; ++j) vout[c][j] = cfma(cb[j], acc[c][j], cmul(ca[j], vin[c][j]));
-    if (flags & SF_AUX) {
-      const S* aux = reinterpret_cast<const S*>(p.aux) + boff;
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        cx<T> tmp[RPT];
-        load_rpt<S, RPT>(aux + size_t(c) * p.R, tmp);
-#pragma unroll
-        for (int j = 0; j < RPT; ++j) vout[c][j] = cfma(cg[j], tmp[j], vout[c][j]);
+        for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], ax[j], vout[j]);
       }
-    }
-    if (flags & SF_WRITE) {
-      S* out = reinterpret_cast<S*>(p.out) + boff;
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        cx<T> tmp[RPT];
-#pragma unroll
-        for (int j = 0; j < RPT; ++j) tmp[j] = vout[c][j];
-        store_rpt<S, RPT>(out + size_t(c) * p.R, tmp);
-      }
-    }
-    if (flags & SF_YACC) {
-      Y* yp = reinterpret_cast<Y*>(p.y) + boff;
-#pragma unroll
-      for (int c = 0; c < 12; ++c)
+      if (flags & SF_WRITE) store_rpt<S, RPT>(reinterpret_cast<S*>(p.out) + boff + size_t(c) * p.R, vout);
+      if (flags & SF_YACC) {
+        Y* yp = reinterpret_cast<Y*>(p.y) + boff + size_t(c) * p.R;
 #pragma unroll
         for (int j = 0; j < RPT; ++j) {
-          Y yv = yp[size_t(c) * p.R + j];
+          Y yv = yp[j];
           cx<T> a = cmake(T(yv.x), T(yv.y));
-          a = cfma(cwi[j], vin[c][j], a);
-          if (flags & SF_BIL_OUT) a = cfma(cwo[j], vout[c][j], a);
+          a = cfma(cwi[j], vin[j], a);
+          if (flags & SF_BIL_OUT) a = cfma(cwo[j], vout[j], a);
           yv.x = a.re;
           yv.y = a.im;
-          yp[size_t(c) * p.R + j] = yv;
+          yp[j] = yv;
         }
+      }
+      if (bil) {
+        // conj(eta_c') (Theta v)_c' with c' the component that Theta maps c to:
+        // gamma_4 swaps upper and lower spins (c' = c +- 6), gamma_5 flips the lower sign.
+        const int cp = (p.theta == 1) ? (c + 6) % 12 : c;
+        const T sg = (p.theta == 2 && c >= 6) ? T(-1) : T(1);
+        cx<T> eta[RPT];
+        if (flags & SF_BIL_CODES) {
+#pragma unroll
+          for (int j = 0; j < RPT; ++j) {
+            const uint32_t k = (code[j] >> (2 * cp)) & 3u;
+            eta[j] = cmake(k == 0 ? T(1) : (k == 2 ? T(-1) : T(0)), k == 1 ? T(1) : (k == 3 ? T(-1) : T(0)));
+          }
+        } else {
+          load_rpt<S, RPT>(reinterpret_cast<const S*>(p.left) + boff + size_t(cp) * p.R, eta);
+        }
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+          si[j] = cfmac(eta[j], cscale(vin[j], sg), si[j]);
+          if (flags & SF_BIL_OUT) so[j] = cfmac(eta[j], cscale(vout[j], sg), so[j]);
+        }
+      }
     }
-    if (flags & (SF_BIL_CODES | SF_BIL_LEFT)) {
+    if (bil) {
 #pragma unroll
       for (int j = 0; j < RPT; ++j) {
-        cx<T> vi[12], vo[12];
-#pragma unroll
-        for (int c = 0; c < 12; ++c) {
-          vi[c] = vin[c][j];
-          vo[c] = vout[c][j];
-        }
-        cx<T> si, so = cmake(T(0), T(0));
-        if (flags & SF_BIL_CODES) {
-          uint32_t code = p.codes[(size_t(rb) * p.V + site) * p.R + r0 + j];
-          si = bil_codes(code, p.theta, vi);
-          if (flags & SF_BIL_OUT) so = bil_codes(code, p.theta, vo);
-        } else {
-          const S* lp = reinterpret_cast<const S*>(p.left) + boff;
-          cx<T> l[12];
-#pragma unroll
-          for (int c = 0; c < 12; ++c) {
-            cx<T> tmp[RPT];
-            load_rpt<S, RPT>(lp + size_t(c) * p.R, tmp);
-            l[c] = tmp[j];
-          }
-          si = bil_left(l, p.theta, vi);
-          if (flags & SF_BIL_OUT) so = bil_left(l, p.theta, vo);
-        }
-        cx<T> contrib = cmul(cwi[j], si);
-        if (flags & SF_BIL_OUT) contrib = cfma(cwo[j], so, contrib);
+        cx<T> contrib = cmul(cwi[j], si[j]);
+        if (flags & SF_BIL_OUT) contrib = cfma(cwo[j], so[j], contrib);
         bre[j] += double(contrib.re);
         bim[j] += double(contrib.im);
       }
@@ -456,22 +444,30 @@ __global__ void __launch_bounds__(128) step_kernel(step_params p) {
 
 }  // namespace
 
-template <typename S, int RPT>
+static long long g_launches = 0;
+long long launch_count() { return g_launches; }
+void count_launch(int n) { g_launches += n; }
+
+template <typename S, int RPT, int MINB>
 static cudaError_t launch_t(const step_params& p, int n_rb, cudaStream_t s) {
   dim3 grid((p.V + p.spc - 1) / p.spc, n_rb);
-  step_kernel<S, RPT><<<grid, 128, 0, s>>>(p);
+  if (p.flags & SF_DAGGER)
+    step_kernel<S, RPT, -1, MINB><<<grid, 128, 0, s>>>(p);
+  else
+    step_kernel<S, RPT, 1, MINB><<<grid, 128, 0, s>>>(p);
+  count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(int prec, int rpt, const step_params& p, int n_rb, cudaStream_t s) {
-  if (prec == 0) return launch_t<double2, 1>(p, n_rb, s);
+// variant: rhs per lane (1, 2, 4) and minimum resident CTAs per SM (register cap)
+cudaError_t launch_step(int prec, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s) {
+  if (prec == 0) return minb >= 3 ? launch_t<double2, 1, 3>(p, n_rb, s) : launch_t<double2, 1, 1>(p, n_rb, s);
   if (prec == 1) {
-    if (rpt == 2) return launch_t<float2, 2>(p, n_rb, s);
-    return launch_t<float2, 1>(p, n_rb, s);
+    if (rpt == 2) return minb >= 3 ? launch_t<float2, 2, 3>(p, n_rb, s) : launch_t<float2, 2, 1>(p, n_rb, s);
+    return minb >= 4 ? launch_t<float2, 1, 4>(p, n_rb, s) : launch_t<float2, 1, 1>(p, n_rb, s);
   }
-  if (rpt == 4) return launch_t<__nv_bfloat162, 4>(p, n_rb, s);
-  if (rpt == 2) return launch_t<__nv_bfloat162, 2>(p, n_rb, s);
-  return launch_t<__nv_bfloat162, 1>(p, n_rb, s);
+  if (rpt == 2) return minb >= 3 ? launch_t<__nv_bfloat162, 2, 3>(p, n_rb, s) : launch_t<__nv_bfloat162, 2, 1>(p, n_rb, s);
+  return minb >= 4 ? launch_t<__nv_bfloat162, 1, 4>(p, n_rb, s) : launch_t<__nv_bfloat162, 1, 1>(p, n_rb, s);
 }
 
 }  // namespace mmc

@@ -48,6 +48,14 @@ class mmc_level_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class mmc_profile_stats(ctypes.Structure):
+    _fields_ = [("step_launches", ctypes.c_longlong), ("step_ms", _d), ("step_bytes", _d), ("step_flops", _d),
+                ("all_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _SIGS = {
     "mmc_create": (_i, [ctypes.POINTER(_vp), _ip, _u64, _i]),
     "mmc_destroy": (_i, [_vp]),
@@ -72,6 +80,11 @@ _SIGS = {
                              ctypes.POINTER(mmc_level_stats), _dp]),
     "mmc_trace_exact": (_i, [_vp, _i, _i, _i, _i, _dp]),
     "mmc_probe_colours": (_i, [_vp, _i, _ip]),
+    "mmc_profile": (_i, [_vp, _i]),
+    "mmc_profile_read": (_i, [_vp, ctypes.POINTER(mmc_profile_stats)]),
+    "mmc_update_gauge": (_i, [_vp, _dp]),
+    "mmc_set_step_variant": (_i, [_vp, _i, _i, _i, _i]),
+    "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
     "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
     "mmc_leja_order": (_i, [_i, _dp, _dp]),
     "mmc_eig": (_i, [_i, _dp, _i, _dp, _dp]),
@@ -251,6 +264,33 @@ def mmc_probe_colours(ctx, reach):
     n = ctypes.c_int()
     _check(lib.mmc_probe_colours(ctx, int(reach), ctypes.byref(n)), ctx)
     return n.value
+
+
+# ---------------------------------------------------------------- profiling
+def mmc_profile(ctx, enable):
+    _check(lib.mmc_profile(ctx, int(enable)), ctx)
+
+
+def mmc_profile_read(ctx):
+    st = mmc_profile_stats()
+    _check(lib.mmc_profile_read(ctx, ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):
+    _check(lib.mmc_set_step_variant(ctx, int(prec), int(rpt), int(minb), int(spc)), ctx)
+
+
+def mmc_autotune(ctx, nrhs, prec):
+    best = (ctypes.c_int * 3)()
+    ms = ctypes.c_double()
+    _check(lib.mmc_autotune(ctx, int(nrhs), int(prec), best, ctypes.byref(ms)), ctx)
+    return {"rpt": best[0], "minb": best[1], "spc": best[2], "ms": ms.value}
+
+
+def mmc_update_gauge(ctx, U):
+    U, p = _cplx(U)
+    _check(lib.mmc_update_gauge(ctx, p), ctx)
 
 
 # ---------------------------------------------------------- host-only helpers
