@@ -134,6 +134,20 @@ int mmc_apply_M(mmc_ctx* ctx, const void* x, void* y, int nrhs, int prec, int da
 int mmc_noise(mmc_ctx* ctx, uint32_t level, uint32_t first, uint32_t tag, int nrhs, int prec,
               void* field, void* stream);
 
+/* mmc_noise without any device allocation, for callers whose device memory is
+ * owned by another allocator (a framework's caching allocator holding the GPU's
+ * memory, a service with a fixed memory budget that forbids allocation once it
+ * runs).  The paper has no counterpart: this is an operational variant.  Same
+ * arguments and output as mmc_noise; nrhs padded to the rhs block must not
+ * exceed 4096 (MMC_ERR_ARG otherwise).  The (level, index) table lives in one
+ * static device array per device (32 KB, held until the process exits) shared
+ * by every call: calls that overlap on the GPU race on it, so the call
+ * synchronises its stream before returning.  The first call on a device looks
+ * up the array's device address (a runtime call that allocates nothing) and
+ * should come before any stream capture.  Never calls cudaMalloc or cudaFree. */
+int mmc_noise_noalloc(mmc_ctx* ctx, uint32_t level, uint32_t first, uint32_t tag, int nrhs, int prec,
+                      void* field, void* stream);
+
 /* ----------------------------------------------------------- polynomials */
 
 /* One GMRES(m) cycle (Sec. 3) of op (MMC_OP_M, or phi_h(M) = M p_h(M) for a single

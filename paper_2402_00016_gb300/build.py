@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmmc.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["stencil.cu", "blas.cu", "api.cu", "levels.cu", "dense.cpp"]
+SOURCES = ["stencil.cu", "blas.cu", "api.cu", "levels.cu", "noalloc.cu", "dense.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -68,6 +68,7 @@ _SIGS = {
     "mmc_unpack": (_i, [_vp, _vp, _i, _i, _dp]),
     "mmc_apply_M": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "mmc_noise": (_i, [_vp, _u32, _u32, _u32, _i, _i, _vp, _vp]),
+    "mmc_noise_noalloc": (_i, [_vp, _u32, _u32, _u32, _i, _i, _vp, _vp]),
     "mmc_gmres_poly": (_i, [_vp, _i, _i, _dp, _ip]),
     "mmc_poly_from_roots": (_i, [_vp, _i, _dp, _ip]),
     "mmc_poly_double": (_i, [_vp, _i, _i, _ip]),
@@ -180,6 +181,12 @@ def mmc_apply_M(ctx, x, y, nrhs, prec, dagger=0, stream=None):
 def mmc_noise(ctx, level, first, tag, nrhs, prec, field, stream=None):
     _check(lib.mmc_noise(ctx, int(level), int(first), int(tag), int(nrhs), int(prec), _ptr(field),
                          _stream(stream)), ctx)
+
+
+def mmc_noise_noalloc(ctx, level, first, tag, nrhs, prec, field, stream=None):
+    """mmc_noise for callers that cannot allocate device memory (static id table, <= 4096 rhs)."""
+    _check(lib.mmc_noise_noalloc(ctx, int(level), int(first), int(tag), int(nrhs), int(prec), _ptr(field),
+                                 _stream(stream)), ctx)
 
 
 # --------------------------------------------------------------- polynomials
