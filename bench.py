@@ -248,6 +248,24 @@ def main():
     est = exact.real + sum(r["value_re"] for r in last)
     stderr = float(np.sqrt(sum(r["var_re"] / r["n"] for r in last)))
 
+    # The plain FP64 single-vector form on the same GPU: same polynomials, deflation and
+    # preconditioner, FP64 storage and arithmetic (FP64 solves), one noise vector per call.
+    # Bounded: one sample per level, extrapolated to the 8/32/128/512 mix.
+    plain = None
+    if rank == 0:
+        per_sample = []
+        for (hi, lo, defl, n, lvl) in plan:
+            torch.cuda.synchronize()
+            t0 = time.time()
+            mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, 1, 900_000, lvl, mmc.MMC_F64, h["in"],
+                                want_samples=False)
+            torch.cuda.synchronize()
+            per_sample.append(time.time() - t0)
+        t_step = sum(n * t for (_, _, _, n, _), t in zip(plan, per_sample))
+        plain = {"value": SAMPLES / t_step, "unit": "samples/s", "seconds_per_sample_by_level": per_sample,
+                 "sample": "one FP64 single-vector sample per level, extrapolated to the 8/32/128/512 mix",
+                 "speedup_of_value": value / (SAMPLES / t_step)}
+
     # CPU baseline: the oracle on a bounded slice of the same workload (rank 0 only)
     cpu = None
     if rank == 0 and world == 1:
@@ -282,10 +300,14 @@ def main():
         "setup_s": {"total": t_setup, "polynomials_and_tuning": t_poly, "deflation": t_defl},
         "autotune": tune,
         "estimate": {"trace_re": est, "stderr": stderr, "exact_last_level": exact.real,
-                     "per_level_var": [r["var_re"] for r in last]},
+                     "per_level_var": [r["var_re"] for r in last],
+                     "per_level_seconds": [r["seconds"] for r in last],
+                     "per_level_matvecs": [r["matvecs"] for r in last]},
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if plain:
+        line["plain_fp64_single_vector"] = plain
     if rank == 0:
         print(json.dumps(line), flush=True)
     mmc.mmc_destroy(ctx)

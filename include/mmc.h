@@ -195,7 +195,8 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arnoldi, double tol_
  * Sec. 8: deflated, polynomial-preconditioned GMRES).  Outer loop in FP64:
  * r = b - M x, deflated correction x += Z Lambda^-1 U^H r, stop when
  * ||r|| <= rel_tol ||b|| per vector; inner right-preconditioned FGMRES(m_inner)
- * in precision prec_inner (MMC_F32 or MMC_BF16 storage, FP32 arithmetic) with
+ * in precision prec_inner (MMC_F32 or MMC_BF16 storage with FP32 arithmetic;
+ * MMC_F64 for the plain FP64 form) with
  * preconditioner p_h(M) (precond_handle, or MMC_ZERO for none).  x is the
  * initial guess on entry.  *iters receives inner iterations, relres_out (nrhs,
  * may be NULL) the final relative residuals. */
@@ -210,7 +211,8 @@ int mmc_solve(mmc_ctx* ctx, const void* b, void* x, int nrhs, double rel_tol, in
  * deflate != 0 (both polynomial) subtracts sum_i c_i (eta^H Theta z_i)(u_i^H eta)
  * with c_i = p_hi(lambda_i) - p_lo(lambda_i) and reports the exact correction
  * (Sec. 7).  prec: storage of the polynomial chains.  For hi = MMC_INV the
- * solves use rel_tol 1e-10, preconditioner `precond` and FGMRES(48).
+ * solves use rel_tol 1e-10, preconditioner `precond` and FGMRES(48), with an
+ * FP32 inner solve, or FP64 throughout when prec = MMC_F64.
  * samples_out (2 n_noise doubles, may be NULL) receives the samples. */
 int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int n_noise,
                     uint32_t first_noise, uint32_t level, int prec, int precond,
@@ -224,6 +226,39 @@ int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec
 
 /* Number of colours of the probing colouring chosen for a reach (L1 distance). */
 int mmc_probe_colours(mmc_ctx* ctx, int reach, int* n_colours);
+
+/* ------------------------------------------------- learned network (no paper section) */
+
+/* A gauge-covariant linear stencil network N approximating M^-1: channel counts
+ * 4 -> 8 -> 8 -> 4 per site (each channel a colour 3-vector, so 12 -> 24 -> 24
+ * -> 12 complex), three layers out(x) = W0 in(x) + sum_mu [Wf_mu U_mu(x) in(x+mu)
+ * + Wb_mu U_mu(x-mu)^+ in(x-mu)] (antiperiodic time phase as in M), no
+ * nonlinearity, so Tr(Theta N) exists and a subtraction with N keeps Eq. 2's
+ * estimator unbiased.  Weights: 1152 complex numbers (2304 doubles), layer
+ * by layer, each [9][C_out][C_in] with index 0 = W0, 1+mu = Wf_mu, 5+mu = Wb_mu.
+ * A network handle (>= MMC_NET_BASE) is accepted as mmc_solve's preconditioner,
+ * as hi or lo of mmc_trace_level (without deflation) and by mmc_trace_exact
+ * (probing with reach 3).  Fields given to the network are MMC_F32. */
+#define MMC_NET_BASE 0x100000
+#define MMC_NET_WEIGHTS 1152
+
+/* Create a network with the given weights (NULL: near the channel embedding of
+ * the identity plus seeded N(0, 0.05^2) entries). */
+int mmc_net_create(mmc_ctx* ctx, const double* weights, uint64_t seed, int* handle);
+int mmc_net_set_weights(mmc_ctx* ctx, int handle, const double* weights);
+int mmc_net_get_weights(mmc_ctx* ctx, int handle, double* weights);
+/* y = N x for nrhs MMC_F32 vectors (inference kernels, FP32 arithmetic). */
+int mmc_net_apply(mmc_ctx* ctx, int handle, const void* x, void* y, int nrhs, void* stream);
+/* Loss L = (1/B) sum_b ||N eta_b - x_b||^2 / ||x_b||^2 on one batch of B = nrhs
+ * MMC_F32 pairs, and grad = dL/dRe W + i dL/dIm W (2304 doubles, may be NULL),
+ * by the training kernels (forward, backward data, weight gradients). */
+int mmc_net_loss_grad(mmc_ctx* ctx, int handle, const void* eta, const void* xs, int nrhs, double* loss,
+                      double* grad);
+/* Train with Adam (lr; betas 0.9, 0.999) for iters steps over mini-batches of
+ * `batch` consecutive pairs (batch divides npairs and is a multiple of the rhs
+ * block); loss_history (iters doubles, may be NULL) receives each step's loss. */
+int mmc_net_train(mmc_ctx* ctx, int handle, const void* eta, const void* xs, int npairs, int batch, int iters,
+                  double lr, double* loss_history);
 
 /* ------------------------------------------------------------ profiling */
 
@@ -249,13 +284,15 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out);
 
 /* Launch variant of the fused step kernel for precision prec: rpt right-hand
  * sides per lane (1, 2; F64 uses 1), minb = minimum resident CTAs per SM asked
- * of the compiler (1: no register cap; 3 or 4: capped), spc = sites per CTA
- * (16..1024, power of two).  Values <= 0 keep the current setting. */
+ * of the compiler for the generic kernel (1: no register cap; 3 or 4: capped),
+ * or 100 + v to select kernel version v (1: generic; 2: rhs block and epilogue
+ * fixed at compile time, for F32/BF16 batches with R = 8 or 16), spc = sites
+ * per CTA (16..1024, power of two).  Values <= 0 keep the current setting. */
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc);
 /* Autotuner: time every step-kernel variant on an nrhs-vector field of
  * precision prec (random data, CUDA events, median of 3 after a warm-up),
- * keep the fastest for that precision and return it (best[3] = rpt, minb, spc)
- * with its time per launch in ms. */
+ * keep the fastest for that precision and return it (best[4] = rpt, minb,
+ * spc, kernel version) with its time per launch in ms. */
 int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms);
 
 /* Replace the device links by a new host field (same layout as mmc_load_gauge)

@@ -62,6 +62,7 @@ int mmc_destroy(mmc_ctx* ctx) {
     if (kv.second.p) cudaFree(kv.second.p);
   if (ctx->links64) cudaFree(ctx->links64);
   if (ctx->links32) cudaFree(ctx->links32);
+  if (ctx->nbr) cudaFree(ctx->nbr);
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
   if (ctx->Z32) cudaFree(ctx->Z32);
@@ -103,6 +104,22 @@ int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiod
         h64[(size_t(s) * 4 + mu) * 9 + k] = make_double2(re, im);
         h32[(size_t(s) * 4 + mu) * 10 + k] = make_float2(float(re), float(im));
       }
+  {
+    // neighbour table [site][8]: x + mu for mu = 0..3, then x - mu (periodic)
+    std::vector<int> nb(size_t(V) * 8);
+    const int* L = ctx->dims;
+    for (int s = 0; s < V; ++s) {
+      int c[4] = {s % L[0], (s / L[0]) % L[1], (s / (L[0] * L[1])) % L[2], s / (L[0] * L[1] * L[2])};
+      int stride = 1;
+      for (int mu = 0; mu < 4; ++mu) {
+        nb[size_t(s) * 8 + mu] = (c[mu] == L[mu] - 1) ? s - (L[mu] - 1) * stride : s + stride;
+        nb[size_t(s) * 8 + 4 + mu] = (c[mu] == 0) ? s + (L[mu] - 1) * stride : s - stride;
+        stride *= L[mu];
+      }
+    }
+    if (!ctx->nbr) CK(cudaMalloc(&ctx->nbr, nb.size() * sizeof(int)));
+    CK(cudaMemcpy(ctx->nbr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   if (!ctx->links64) CK(cudaMalloc(&ctx->links64, h64.size() * sizeof(double2)));
   if (!ctx->links32) CK(cudaMalloc(&ctx->links32, h32.size() * sizeof(float2)));
   CK(cudaMemcpy(ctx->links64, h64.data(), h64.size() * sizeof(double2), cudaMemcpyHostToDevice));
@@ -157,6 +174,10 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out) {
 
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
   if (!ctx || prec < 0 || prec > 2) return MMC_ERR_ARG;
+  if (minb >= 100) {  // minb = 100 + v selects kernel version v (1: generic, 2: compile-time rhs block)
+    ctx->var_ver[prec] = minb - 100;
+    minb = 0;
+  }
   if (rpt > 0) {
     if (rpt != 1 && rpt != 2) RET(MMC_ERR_ARG, "rpt must be 1 or 2");
     ctx->var_rpt[prec] = prec == MMC_F64 ? 1 : rpt;
@@ -190,12 +211,15 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   const int minbs[3] = {1, 3, 4};
   const int spcs[4] = {32, 64, 128, 256};
   double best_ms = 1e300;
-  int br = ctx->var_rpt[prec], bm = ctx->var_minb[prec], bs = ctx->spc_step;
+  int br = ctx->var_rpt[prec], bm = ctx->var_minb[prec], bs = ctx->spc_step, bv = ctx->var_ver[prec];
+  const bool v2ok = prec != MMC_F64 && (g.R == 8 || g.R == 16);
+  for (int ver = 1; ver <= (v2ok ? 2 : 1); ++ver)
   for (int ri = 0; ri < 2; ++ri) {
     if (prec == MMC_F64 && rpts[ri] != 1) continue;
     if (rpts[ri] > g.R) continue;
-    for (int mi = 0; mi < 3; ++mi) {
+    for (int mi = 0; mi < (ver == 2 ? 1 : 3); ++mi) {  // the v2 kernel fixes its register cap per rpt
       for (int si = 0; si < 4; ++si) {
+        ctx->var_ver[prec] = ver;
         ctx->var_rpt[prec] = rpts[ri];
         ctx->var_minb[prec] = minbs[mi];
         ctx->spc_step = spcs[si];
@@ -216,6 +240,7 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
           br = rpts[ri];
           bm = minbs[mi];
           bs = spcs[si];
+          bv = ver;
         }
       }
     }
@@ -225,10 +250,12 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   ctx->var_rpt[prec] = br;
   ctx->var_minb[prec] = bm;
   ctx->spc_step = bs;
+  ctx->var_ver[prec] = bv;
   if (best) {
     best[0] = br;
     best[1] = bm;
     best[2] = bs;
+    best[3] = bv;
   }
   if (ms_out) *ms_out = best_ms;
   return MMC_OK;

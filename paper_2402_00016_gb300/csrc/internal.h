@@ -31,6 +31,16 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Learned gauge-covariant stencil network: channels 4 -> 8 -> 8 -> 4, three layers,
+// weights per layer [9][C_out][C_in] complex (host FP64 copy, device FP32 copy).
+struct Net {
+  std::vector<std::complex<double>> w;  // 1152 complex
+  float2* dw = nullptr;                 // device copy, same order
+};
+constexpr int kNetCh[4] = {4, 8, 8, 4};
+constexpr int kNetWeights = 9 * (8 * 4 + 8 * 8 + 4 * 8);
+constexpr int kNetBase = 0x100000;
+
 }  // namespace host
 }  // namespace mmc
 
@@ -46,6 +56,7 @@ struct mmc_ctx {
   void* links64 = nullptr;
   void* links32 = nullptr;
   std::vector<mmc::host::Poly> polys;
+  std::vector<mmc::host::Net> nets;
   // deflation data (FP64 single-vector fields [site][12])
   int k_defl = 0;
   std::vector<mmc::cd> lambda;
@@ -59,6 +70,8 @@ struct mmc_ctx {
   int spc_step = 64;  // sites per CTA of the step kernel (all precisions: partial buffers depend on it)
   int var_rpt[3] = {1, 2, 2};
   int var_minb[3] = {1, 1, 1};
+  int var_ver[3] = {1, 2, 2};  // 1: generic step_kernel, 2: step2_kernel (R = 8, 16; F32, BF16)
+  int* nbr = nullptr;          // device neighbour table [site][8]
   // profiling (mmc_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -220,6 +233,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     p.partial = run.partial;
     p.links = run.prec == MMC_F64 ? ctx->links64 : ctx->links32;
     p.rb_len = run.rb_len;
+    p.nbr = ctx->nbr;
     p.step = int(k);
     p.V = ctx->V;
     p.R = g.R;
@@ -239,7 +253,14 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       TRY(prof_event(ctx, &e1));
       CK(cudaEventRecord(e0, s));
     }
-    CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec], p, g.nrb, s));
+    bool done = false;
+    if (ctx->var_ver[run.prec] == 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      cudaError_t e2 = cudaSuccess;
+      done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, p, g.nrb, s, &e2)
+                                 : mmc::launch_step2_bf16(g.R, rpt, p, g.nrb, s, &e2);
+      CK(e2);
+    }
+    if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec], p, g.nrb, s));
     if (ctx->prof) {
       CK(cudaEventRecord(e1, s));
       ctx->ev_pending.push_back({e0, e1});
@@ -527,6 +548,10 @@ inline int apply_op_f64(mmc_ctx* ctx, int op_handle, const void* in, void* out, 
   TRY(apply_poly_impl(ctx, op_handle, in, nrhs, MMC_F64, ACC_Y, T, base, s));
   return apply_M_impl(ctx, T, out, nrhs, MMC_F64, false, s);
 }
+
+// learned network (learned.cu)
+bool is_net(const mmc_ctx* ctx, int h);
+int net_apply(mmc_ctx* ctx, int h, const void* x, void* y, int nrhs, cudaStream_t s, float2** acts);
 
 inline int check_ctx(mmc_ctx* ctx) {
   if (!ctx) return MMC_ERR_ARG;

@@ -20,6 +20,11 @@ void count_launch(int n = 1);
 // minb: minimum resident CTAs per SM asked of the compiler (caps registers).
 cudaError_t launch_step(int prec, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s);
 
+// Step kernel v2 (stencil2_*.cu): compile-time rhs block R (8 or 16) and epilogue
+// mode; returns false (nothing launched) when the flags or R need step_kernel.
+bool launch_step2_f32(int R, int rpt, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
+bool launch_step2_bf16(int R, int rpt, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
+
 // Z(4) noise (Sec. 1) into a field of precision prec and/or packed codes.
 // ids[r] = (level, noise index) for rhs r (npad entries, device); entries with
 // level == 0xffffffff give zero vectors (padding).
@@ -72,6 +77,20 @@ cudaError_t launch_vec_proj(int prec, geom g, const double2* Vv, int k, const vo
                             cudaStream_t s);
 cudaError_t launch_vec_update(int prec, geom g, const double2* Vv, int k, const double2* coef, void* f,
                               cudaStream_t s);
+
+// Learned stencil network layers (net.cu).  Activations: blocked layout with 3*C
+// components per site; links: the FP32 links of the context.
+struct net_geom {
+  int V, R, nrb, npad;
+  int L[4];
+  const void* links;
+};
+// out = layer(in) for (ci, co) in {(4,8), (8,8), (8,4), (4,4)}; W: 9 x co x ci complex FP32.
+cudaError_t launch_net_layer(const net_geom& g, int ci, int co, const float2* in, const float2* W, float2* out,
+                             cudaStream_t s);
+// partial[b][9][co][ci] over b = rb * nbx + bx: sum delta conj(feature) (weight gradients).
+cudaError_t launch_net_wgrad(const net_geom& g, int ci, int co, const float2* in, const float2* delta, int spc,
+                             double2* partial, cudaStream_t s);
 
 // Complex small-matrix kernels on the device for the Arnoldi bookkeeping.
 // hcol[i] = h1[i] + h2[i] for i < n (per rhs), written into H column storage.

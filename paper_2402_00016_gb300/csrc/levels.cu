@@ -91,19 +91,21 @@ int deflate_residual(mmc_ctx* ctx, const geom& g, const void* r, void* x, cudaSt
 int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int precond, int prec_inner, int m,
                int max_outer, int* iters, std::vector<double>& rel, cudaStream_t s) {
   const geom g = make_geom(ctx, nrhs);
-  const size_t f64 = field_bytes(g, MMC_F64), f32 = field_bytes(g, MMC_F32);
-  void *r, *r32, *Vb, *Zb, *e32, *e64;
+  // inner precision: F32 basis for F32/BF16 inner solves, F64 basis for the plain FP64 form
+  const int ip = prec_inner == MMC_F64 ? MMC_F64 : MMC_F32;
+  const size_t f64 = field_bytes(g, MMC_F64), fi = field_bytes(g, ip);
+  const size_t ebytes = elem_bytes(ip);
+  void *r, *Vb, *Zb = nullptr, *ei, *e64;
   TRY(scratch(ctx, "sv_r", f64, &r));
-  TRY(scratch(ctx, "sv_r32", f32, &r32));
-  TRY(scratch(ctx, "sv_V", f32 * (m + 1), &Vb));
-  if (precond != MMC_ZERO) TRY(scratch(ctx, "sv_Z", f32 * m, &Zb));
-  TRY(scratch(ctx, "sv_e32", f32, &e32));
+  TRY(scratch(ctx, ip == MMC_F64 ? "sv_V64" : "sv_V", fi * (m + 1), &Vb));
+  if (precond != MMC_ZERO) TRY(scratch(ctx, ip == MMC_F64 ? "sv_Z64" : "sv_Z", fi * m, &Zb));
+  TRY(scratch(ctx, ip == MMC_F64 ? "sv_e64i" : "sv_e32", fi, &ei));
   TRY(scratch(ctx, "sv_e64", f64, &e64));
   std::vector<double> bn2, rn2;
   TRY(norms2(ctx, MMC_F64, g, b, bn2, s));
   int inner = 0;
   rel.assign(nrhs, 0.0);
-  const size_t stride32 = size_t(g.npad) * g.V * 12;
+  const size_t stride = size_t(g.npad) * g.V * 12;  // elements per basis field
   for (int outer = 0; outer <= max_outer; ++outer) {
     TRY(residual_f64(ctx, g, b, x, r, s));
     if (ctx->k_defl > 0) {
@@ -122,33 +124,34 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
       return MMC_OK;
     }
     if (outer == max_outer) break;
-    // inner right-preconditioned FGMRES(m) cycle in FP32 on M e = r
-    CK(mmc::launch_convert(MMC_F32, Vb, MMC_F64, r, g, s));
+    // inner right-preconditioned FGMRES(m) cycle on M e = r
+    CK(mmc::launch_convert(ip, Vb, MMC_F64, r, g, s));
     auto op = [&](const void* vj, void* w) -> int {
       const void* zj = vj;
       if (precond != MMC_ZERO) {
-        const size_t j = (reinterpret_cast<const char*>(vj) - reinterpret_cast<const char*>(Vb)) / (stride32 * 8);
-        void* zdst = reinterpret_cast<char*>(Zb) + j * stride32 * 8;
+        const size_t j = (reinterpret_cast<const char*>(vj) - reinterpret_cast<const char*>(Vb)) / (stride * ebytes);
+        void* zdst = reinterpret_cast<char*>(Zb) + j * stride * ebytes;
         Run base;
         base.g = g;
-        if (prec_inner == MMC_BF16) {
+        if (is_net(ctx, precond)) {
+          if (ip != MMC_F32) RET(MMC_ERR_ARG, "mmc_solve: the learned preconditioner needs an FP32 inner solve");
+          TRY(net_apply(ctx, precond, vj, zdst, g.npad, s, nullptr));
+        } else if (prec_inner == MMC_BF16) {
           void* v16;
-          void* y32;
           TRY(scratch(ctx, "sv_v16", field_bytes(g, MMC_BF16), &v16));
-          TRY(scratch(ctx, "sv_y32", f32, &y32));
           CK(mmc::launch_convert(MMC_BF16, v16, MMC_F32, vj, g, s));
           base.prec = MMC_BF16;
           TRY(apply_poly_impl(ctx, precond, v16, g.npad, MMC_BF16, ACC_Y, zdst, base, s));
         } else {
-          base.prec = MMC_F32;
-          TRY(apply_poly_impl(ctx, precond, vj, g.npad, MMC_F32, ACC_Y, zdst, base, s));
+          base.prec = ip;
+          TRY(apply_poly_impl(ctx, precond, vj, g.npad, ip, ACC_Y, zdst, base, s));
         }
         zj = zdst;
       }
-      return apply_M_impl(ctx, zj, w, g.npad, MMC_F32, false, s);
+      return apply_M_impl(ctx, zj, w, g.npad, ip, false, s);
     };
     ArnoldiOut ao;
-    TRY(arnoldi_cgs2(ctx, g, MMC_F32, Vb, m, op, ao, s));
+    TRY(arnoldi_cgs2(ctx, g, ip, Vb, m, op, ao, s));
     inner += m;
     std::vector<cd> ycoef(size_t(m) * g.npad, cd(0, 0));
     for (int rr = 0; rr < g.npad; ++rr) {
@@ -161,13 +164,13 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
     }
     void* dy;
     TRY(upload(ctx, "sv_y", ycoef, &dy, s));
-    CK(cudaMemsetAsync(e32, 0, f32, s));
-    CK(mmc::launch_basis_update(MMC_F32, g, precond != MMC_ZERO ? Zb : Vb, stride32, m, (const double2*)dy, e32, s));
-    CK(mmc::launch_convert(MMC_F64, e64, MMC_F32, e32, g, s));
+    CK(cudaMemsetAsync(ei, 0, fi, s));
+    CK(mmc::launch_basis_update(ip, g, precond != MMC_ZERO ? Zb : Vb, stride, m, (const double2*)dy, ei, s));
+    if (ip != MMC_F64) CK(mmc::launch_convert(MMC_F64, e64, ip, ei, g, s));
     std::vector<cd> one(g.npad, cd(1, 0));
     void* d1;
     TRY(upload(ctx, "sv_one", one, &d1, s));
-    CK(mmc::launch_axpby(MMC_F64, g, (const double2*)d1, e64, (const double2*)d1, x, s));
+    CK(mmc::launch_axpby(MMC_F64, g, (const double2*)d1, ip == MMC_F64 ? ei : e64, (const double2*)d1, x, s));
   }
   if (iters) *iters = inner;
   RET(MMC_ERR_NOCONV, "mmc_solve: relative residual above tolerance after max_outer cycles");
@@ -445,8 +448,9 @@ int mmc_solve(mmc_ctx* ctx, const void* b, void* x, int nrhs, double rel_tol, in
   TRY(check_ctx(ctx));
   if (!b || !x || b == x || nrhs < 1 || m_inner < 1 || max_outer < 0 || !(rel_tol > 0))
     RET(MMC_ERR_ARG, "mmc_solve: bad argument");
-  if (prec_inner != MMC_F32 && prec_inner != MMC_BF16) RET(MMC_ERR_ARG, "mmc_solve: prec_inner must be F32 or BF16");
-  if (precond != MMC_ZERO && !valid_poly(ctx, precond)) RET(MMC_ERR_ARG, "mmc_solve: bad preconditioner handle");
+  if (prec_inner < MMC_F64 || prec_inner > MMC_BF16) RET(MMC_ERR_ARG, "mmc_solve: bad prec_inner");
+  if (precond != MMC_ZERO && !valid_poly(ctx, precond) && !is_net(ctx, precond))
+    RET(MMC_ERR_ARG, "mmc_solve: bad preconditioner handle");
   std::vector<double> rel;
   int rc = solve_impl(ctx, b, x, nrhs, rel_tol, precond, prec_inner, m_inner, max_outer, iters, rel, ctx->stream);
   if (relres_out)
@@ -460,8 +464,11 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
   TRY(check_ctx(ctx));
   if (!out || n_noise < 1 || prec < 0 || prec > 2 || theta_op < 0 || theta_op > 2)
     RET(MMC_ERR_ARG, "mmc_trace_level: bad argument");
-  if (!(hi == MMC_INV || valid_poly(ctx, hi)) || !(lo == MMC_ZERO || valid_poly(ctx, lo)))
+  if (!(hi == MMC_INV || valid_poly(ctx, hi) || is_net(ctx, hi)) ||
+      !(lo == MMC_ZERO || valid_poly(ctx, lo) || is_net(ctx, lo)))
     RET(MMC_ERR_ARG, "mmc_trace_level: bad level operands");
+  if (deflate && (is_net(ctx, hi) || is_net(ctx, lo)))
+    RET(MMC_ERR_ARG, "mmc_trace_level: deflation needs polynomial operands (c_i = p_hi(lambda_i) - p_lo(lambda_i))");
   const auto t0 = std::chrono::steady_clock::now();
   const long long mv0 = ctx->matvecs;
   cudaStream_t s = ctx->stream;
@@ -478,6 +485,21 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
   CK(mmc::launch_noise(prec, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, X, (uint32_t*)codes, s));
   std::vector<cd> x(g.npad, cd(0, 0));
   auto poly_bilinear = [&](int h, double sign) -> int {
+    if (is_net(ctx, h)) {
+      // learned operand: y = N eta in FP32, then eta^H Theta y
+      void *x32, *y32;
+      TRY(scratch(ctx, "lv_x32", field_bytes(g, MMC_F32), &x32));
+      TRY(scratch(ctx, "lv_y32", field_bytes(g, MMC_F32), &y32));
+      CK(mmc::launch_noise(MMC_F32, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, x32, nullptr, s));
+      TRY(net_apply(ctx, h, x32, y32, g.npad, s, nullptr));
+      const int nb2 = (g.V + kSpc - 1) / kSpc;
+      CK(cudaMemsetAsync(part, 0, size_t(nb2) * g.npad * sizeof(double2), s));
+      CK(mmc::launch_bilinear_codes(MMC_F32, g, (const uint32_t*)codes, theta_op, y32, kSpc, (double2*)part, s));
+      std::vector<cd> v;
+      TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, g.npad, v, s));
+      for (int r = 0; r < g.npad; ++r) x[r] += sign * v[r];
+      return MMC_OK;
+    }
     CK(cudaMemsetAsync(part, 0, size_t(nbx) * g.npad * sizeof(double2), s));
     Run base;
     base.g = g;
@@ -500,7 +522,9 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     CK(cudaMemsetAsync(x64, 0, field_bytes(g, MMC_F64), s));
     std::vector<double> rel;
     int its = 0;
-    TRY(solve_impl(ctx, b64, x64, n_noise, 1e-10, precond, MMC_F32, 48, 400, &its, rel, s));
+    // the plain FP64 form (prec = MMC_F64) solves in FP64 throughout; otherwise FP32 inner
+    TRY(solve_impl(ctx, b64, x64, n_noise, 1e-10, precond, prec == MMC_F64 ? MMC_F64 : MMC_F32, 48, 400, &its, rel,
+                   s));
     const int nb2 = (g.V + kSpc - 1) / kSpc;
     CK(cudaMemsetAsync(part, 0, size_t(nb2) * g.npad * sizeof(double2), s));
     CK(mmc::launch_bilinear_codes(MMC_F64, g, (const uint32_t*)codes, theta_op, x64, kSpc, (double2*)part, s));
@@ -587,12 +611,14 @@ int mmc_probe_colours(mmc_ctx* ctx, int reach, int* n_colours) {
 
 int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec, double* out) {
   TRY(check_ctx(ctx));
-  if (!valid_poly(ctx, handle) || !out || prec < 0 || prec > 2 || theta_op < 0 || theta_op > 2)
+  const bool net = is_net(ctx, handle);
+  if (!(valid_poly(ctx, handle) || net) || !out || prec < 0 || prec > 2 || theta_op < 0 || theta_op > 2)
     RET(MMC_ERR_ARG, "mmc_trace_exact: bad argument");
+  if (net) prec = MMC_F32;  // the network runs in FP32
   cudaStream_t s = ctx->stream;
   Colouring col;
   if (method == MMC_EXACT_PROBE) {
-    col = find_colouring(ctx->dims, ctx->V, poly_degree(ctx, handle));
+    col = find_colouring(ctx->dims, ctx->V, net ? 3 : poly_degree(ctx, handle));
   } else {
     col.n = ctx->V;
     col.colour.resize(ctx->V);
@@ -610,6 +636,7 @@ int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec
   TRY(scratch(ctx, "ex_part", size_t(nbx) * g.npad * sizeof(double2), &part));
   CK(cudaMemsetAsync(part, 0, size_t(nbx) * g.npad * sizeof(double2), s));
   std::vector<int2> pr(g.npad);
+  cd net_total(0, 0);
   for (long long p0 = 0; p0 < nprobe; p0 += batch) {
     int nb = int(std::min<long long>(batch, nprobe - p0));
     for (int r = 0; r < g.npad; ++r) {
@@ -618,6 +645,19 @@ int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec
     }
     CK(cudaMemcpyAsync(dpr, pr.data(), pr.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     CK(mmc::launch_probe(prec, g, (const int*)dcol, (const int2*)dpr, X, s));
+    if (net) {
+      void* Y;
+      TRY(scratch(ctx, "ex_Y", field_bytes(g, MMC_F32), &Y));
+      TRY(net_apply(ctx, handle, X, Y, g.npad, s, nullptr));
+      const int nb2 = (g.V + kSpc - 1) / kSpc;
+      void* p2;
+      TRY(scratch(ctx, "ex_part2", size_t(nb2) * g.npad * sizeof(double2), &p2));
+      CK(mmc::launch_multidot(MMC_F32, g, X, 0, 1, Y, theta_op, kSpc, (double2*)p2, s));
+      std::vector<cd> v;
+      TRY(reduce_to_host(ctx, (double2*)p2, nb2, 1, g.npad, v, s));
+      for (auto& z : v) net_total += z;
+      continue;
+    }
     Run base;
     base.g = g;
     base.prec = prec;
@@ -628,10 +668,12 @@ int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec
     TRY(apply_poly_impl(ctx, handle, X, g.npad, prec, ACC_BIL, nullptr, base, s));
     CK(cudaStreamSynchronize(s));  // probe table is rewritten by the next batch
   }
-  std::vector<cd> v;
-  TRY(reduce_to_host(ctx, (double2*)part, nbx, 1, g.npad, v, s));
-  cd tot(0, 0);
-  for (auto& z : v) tot += z;
+  cd tot = net_total;
+  if (!net) {
+    std::vector<cd> v;
+    TRY(reduce_to_host(ctx, (double2*)part, nbx, 1, g.npad, v, s));
+    for (auto& z : v) tot += z;
+  }
   out[0] = tot.real();
   out[1] = tot.imag();
   return MMC_OK;

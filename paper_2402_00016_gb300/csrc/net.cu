@@ -61,7 +61,7 @@ __device__ __forceinline__ void feature(const float2* in, const float2* links, c
     return;
   }
   float2 u[9];
-  load_link32(g.links, fwd ? site : src, mu, u);
+  load_link32(links, fwd ? site : src, mu, u);
 #pragma unroll
   for (int i = 0; i < CI; ++i)
 #pragma unroll

@@ -1,0 +1,10 @@
+// Step kernel v2 instantiations for BF16 storage (R = 8, 16; one or two rhs per lane).
+#include "stencil2.cuh"
+
+namespace mmc {
+bool launch_step2_bf16(int R, int rpt, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err) {
+  if (R == 16) return rpt == 1 ? sten2::launch2<__nv_bfloat162, 16, 1>(p, n_rb, s, err) : sten2::launch2<__nv_bfloat162, 16, 2>(p, n_rb, s, err);
+  if (R == 8) return rpt == 1 ? sten2::launch2<__nv_bfloat162, 8, 1>(p, n_rb, s, err) : sten2::launch2<__nv_bfloat162, 8, 2>(p, n_rb, s, err);
+  return false;
+}
+}  // namespace mmc

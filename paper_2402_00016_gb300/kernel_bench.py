@@ -1,0 +1,66 @@
+"""Throughput of the fused step kernel on one configuration (a small driver for
+profilers and for tuning): a polynomial level chain eta^H Theta p(M) eta on a
+synthetic field, timed with CUDA events.
+
+python -m paper_2402_00016_gb300.kernel_bench --dims 16 16 16 16 --nrhs 128 --prec bf16 --degree 8 --reps 3
+"""
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs=4, default=[16, 16, 16, 16])
+    ap.add_argument("--nrhs", type=int, default=128)
+    ap.add_argument("--prec", default="bf16", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--degree", type=int, default=8)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--rpt", type=int, default=0)
+    ap.add_argument("--minb", type=int, default=0)
+    ap.add_argument("--spc", type=int, default=0)
+    a = ap.parse_args(argv)
+    import torch
+    import synth
+    from paper_2402_00016_gb300 import build
+    build.build()
+    from paper_2402_00016_gb300 import mmc
+    prec = mmc.PREC[a.prec]
+    ctx = mmc.mmc_create(a.dims, seed=3, device=0)
+    try:
+        mmc.mmc_load_gauge(ctx, synth.random_gauge(a.dims, 0.25, 1), 0.1565, 1)
+        mmc.mmc_set_step_variant(ctx, prec, a.rpt, a.minb, a.spc)
+        # fixed Leja-ordered roots on a circle around 1 (no setup kernels before the chain)
+        m = a.degree + 1
+        theta = mmc.mmc_leja_order(1.0 + 0.8 * np.exp(2j * np.pi * (np.arange(m) + 0.5) / m))
+        h = mmc.mmc_poly_from_roots(ctx, theta)
+        mmc.mmc_trace_level(ctx, h, mmc.MMC_ZERO, 0, 0, a.nrhs, 0, 1, prec)  # warm-up
+        mmc.mmc_profile(ctx, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(a.reps):
+            mmc.mmc_trace_level(ctx, h, mmc.MMC_ZERO, 0, 0, a.nrhs, a.nrhs * (r + 1), 1, prec)
+        e1.record()
+        torch.cuda.synchronize()
+        p = mmc.mmc_profile_read(ctx)
+        vol = int(np.prod(a.dims))
+        out = {"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "degree": a.degree,
+               "step_launches": p["step_launches"], "avg_launch_ms": p["step_ms"] / max(1, p["step_launches"]),
+               "algorithmic_GBps": p["step_bytes"] / p["step_ms"] / 1e6 if p["step_ms"] else 0,
+               "TFLOPs": p["step_flops"] / p["step_ms"] / 1e9 if p["step_ms"] else 0,
+               "ps_per_site_rhs": 1e9 * p["step_ms"] / max(1, p["step_launches"]) / (vol * a.nrhs),
+               "wall_ms": e0.elapsed_time(e1)}
+        print(json.dumps(out), flush=True)
+    finally:
+        mmc.mmc_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()

@@ -23,6 +23,8 @@ MMC_INV = -2
 MMC_TAG_NOISE = 0x4E4F4953
 MMC_TAG_GMRES = 0x474D5253
 MMC_TAG_ARNOLDI = 0x4445464C
+MMC_NET_BASE = 0x100000
+MMC_NET_WEIGHTS = 1152
 PREC = {"f64": MMC_F64, "f32": MMC_F32, "bf16": MMC_BF16}
 THETA = {"1": MMC_THETA_ONE, "g4": MMC_THETA_G4, "g5": MMC_THETA_G5}
 ERRORS = {-1: "MMC_ERR_ARG", -2: "MMC_ERR_NOMEM", -3: "MMC_ERR_CUDA", -4: "MMC_ERR_BREAKDOWN",
@@ -81,6 +83,12 @@ _SIGS = {
                              ctypes.POINTER(mmc_level_stats), _dp]),
     "mmc_trace_exact": (_i, [_vp, _i, _i, _i, _i, _dp]),
     "mmc_probe_colours": (_i, [_vp, _i, _ip]),
+    "mmc_net_create": (_i, [_vp, _dp, _u64, _ip]),
+    "mmc_net_set_weights": (_i, [_vp, _i, _dp]),
+    "mmc_net_get_weights": (_i, [_vp, _i, _dp]),
+    "mmc_net_apply": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
+    "mmc_net_loss_grad": (_i, [_vp, _i, _vp, _vp, _i, _dp, _dp]),
+    "mmc_net_train": (_i, [_vp, _i, _vp, _vp, _i, _i, _i, _d, _dp]),
     "mmc_profile": (_i, [_vp, _i]),
     "mmc_profile_read": (_i, [_vp, ctypes.POINTER(mmc_profile_stats)]),
     "mmc_update_gauge": (_i, [_vp, _dp]),
@@ -273,6 +281,67 @@ def mmc_probe_colours(ctx, reach):
     return n.value
 
 
+# ----------------------------------------------------------- learned network
+def _weights_in(weights):
+    """Accept a list of three (9, C_out, C_in) complex arrays or a flat complex array."""
+    if isinstance(weights, (list, tuple)):
+        weights = np.concatenate([np.asarray(w, dtype=np.complex128).ravel() for w in weights])
+    w = np.ascontiguousarray(weights, dtype=np.complex128).ravel()
+    if w.size != MMC_NET_WEIGHTS:
+        raise ValueError("expected %d complex weights" % MMC_NET_WEIGHTS)
+    return w
+
+
+def _weights_out(flat):
+    shapes = [(9, 8, 4), (9, 8, 8), (9, 4, 8)]
+    out, off = [], 0
+    for sh in shapes:
+        n = int(np.prod(sh))
+        out.append(flat[off:off + n].reshape(sh))
+        off += n
+    return out
+
+
+def mmc_net_create(ctx, weights=None, seed=0):
+    h = ctypes.c_int()
+    if weights is None:
+        _check(lib.mmc_net_create(ctx, None, int(seed), ctypes.byref(h)), ctx)
+    else:
+        w = _weights_in(weights)
+        _check(lib.mmc_net_create(ctx, w.ctypes.data_as(_dp), int(seed), ctypes.byref(h)), ctx)
+    return h.value
+
+
+def mmc_net_set_weights(ctx, handle, weights):
+    w = _weights_in(weights)
+    _check(lib.mmc_net_set_weights(ctx, int(handle), w.ctypes.data_as(_dp)), ctx)
+
+
+def mmc_net_get_weights(ctx, handle):
+    out = np.zeros(2 * MMC_NET_WEIGHTS)
+    _check(lib.mmc_net_get_weights(ctx, int(handle), out.ctypes.data_as(_dp)), ctx)
+    return _weights_out(out[0::2] + 1j * out[1::2])
+
+
+def mmc_net_apply(ctx, handle, x, y, nrhs, stream=None):
+    _check(lib.mmc_net_apply(ctx, int(handle), _ptr(x), _ptr(y), int(nrhs), _stream(stream)), ctx)
+
+
+def mmc_net_loss_grad(ctx, handle, eta, xs, nrhs):
+    loss = ctypes.c_double()
+    g = np.zeros(2 * MMC_NET_WEIGHTS)
+    _check(lib.mmc_net_loss_grad(ctx, int(handle), _ptr(eta), _ptr(xs), int(nrhs), ctypes.byref(loss),
+                                 g.ctypes.data_as(_dp)), ctx)
+    return loss.value, _weights_out(g[0::2] + 1j * g[1::2])
+
+
+def mmc_net_train(ctx, handle, eta, xs, npairs, batch, iters, lr):
+    hist = np.zeros(max(1, int(iters)))
+    _check(lib.mmc_net_train(ctx, int(handle), _ptr(eta), _ptr(xs), int(npairs), int(batch), int(iters),
+                             float(lr), hist.ctypes.data_as(_dp)), ctx)
+    return hist[: int(iters)]
+
+
 # ---------------------------------------------------------------- profiling
 def mmc_profile(ctx, enable):
     _check(lib.mmc_profile(ctx, int(enable)), ctx)
@@ -289,10 +358,10 @@ def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):
 
 
 def mmc_autotune(ctx, nrhs, prec):
-    best = (ctypes.c_int * 3)()
+    best = (ctypes.c_int * 4)()
     ms = ctypes.c_double()
     _check(lib.mmc_autotune(ctx, int(nrhs), int(prec), best, ctypes.byref(ms)), ctx)
-    return {"rpt": best[0], "minb": best[1], "spc": best[2], "ms": ms.value}
+    return {"rpt": best[0], "minb": best[1], "spc": best[2], "version": best[3], "ms": ms.value}
 
 
 def mmc_update_gauge(ctx, U):

@@ -182,3 +182,25 @@ def test_double_poly(mmc, lat):
         eta = noise.z4_noise(lat.dims, 5, j, 4).ravel()
         want = krylov.apply_double(lat.op, th_in, th_out, eta)
         assert np.linalg.norm(got[j] - want) / np.linalg.norm(want) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("ver,rpt", [(1, 1), (1, 2), (2, 1), (2, 2)])
+@pytest.mark.parametrize("nrhs", [5, 21])
+def test_step_kernel_variants(mmc, lat, prec, ver, rpt, nrhs):
+    """Both step-kernel versions (generic, compile-time rhs block) and lane widths give M x."""
+    mmc.mmc_set_step_variant(lat.ctx, prec, rpt, 100 + ver, 0)
+    try:
+        rng_x = synth.random_spinor(lat.dims, 9, nrhs).transpose(6, 0, 1, 2, 3, 4, 5).reshape(nrhs, -1)
+        x = mmc.new_field(lat.ctx, nrhs, prec)
+        y = mmc.new_field(lat.ctx, nrhs, prec)
+        mmc.mmc_pack(lat.ctx, rng_x, nrhs, prec, x)
+        xin = mmc.mmc_unpack(lat.ctx, x, nrhs, prec, lat.V)
+        mmc.mmc_apply_M(lat.ctx, x, y, nrhs, prec, 0)
+        got = mmc.mmc_unpack(lat.ctx, y, nrhs, prec, lat.V)
+        tol = 1e-5 if prec == 1 else BF16_BOUND
+        for j in range(nrhs):
+            want = lat.op(xin[j])
+            assert np.linalg.norm(got[j] - want) / np.linalg.norm(want) < tol
+    finally:
+        mmc.mmc_set_step_variant(lat.ctx, prec, 2, 102, 0)
