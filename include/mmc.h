@@ -189,6 +189,19 @@ int mmc_apply_poly(mmc_ctx* ctx, int handle, const void* x, void* y, int nrhs, i
 int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arnoldi, double tol_accept,
                 double* lambda_out, int* k_accepted);
 
+/* Replace the deflation data by k caller-given eigenpairs (Sec. 7): lambda (2k
+ * doubles), right vectors Z and left vectors U (k vectors each, canonical host
+ * order, complex128), with U^H Z = I expected (not checked).  For a deflation
+ * space from elsewhere, or one saved by mmc_get_deflation (checkpoint). */
+int mmc_set_deflation(mmc_ctx* ctx, int k, const double* lambda, const double* Z, const double* U);
+/* Copy the current deflation data out (any pointer may be NULL; *k always set). */
+int mmc_get_deflation(mmc_ctx* ctx, int* k, double* lambda, double* Z, double* U);
+/* FP32 and BF16 levels project noise on the deflation vectors with tcgen05 tensor cores
+ * (one BF16 GEMM, FP32 accumulation, k <= 128) when enabled (default), from BF16
+ * copies of Theta z_i and u_i that also give the exact correction; otherwise on
+ * CUDA cores from FP32 copies. */
+int mmc_set_tensor_projections(mmc_ctx* ctx, int enable);
+
 /* ---------------------------------------------------------------- solves */
 
 /* Solve M x = b for nrhs FP64 fields (Sec. 1: the solves of Hutchinson's method;
@@ -211,7 +224,8 @@ int mmc_solve(mmc_ctx* ctx, const void* b, void* x, int nrhs, double rel_tol, in
  * deflate != 0 (both polynomial) subtracts sum_i c_i (eta^H Theta z_i)(u_i^H eta)
  * with c_i = p_hi(lambda_i) - p_lo(lambda_i) and reports the exact correction
  * (Sec. 7).  prec: storage of the polynomial chains.  For hi = MMC_INV the
- * solves use rel_tol 1e-10, preconditioner `precond` and FGMRES(48), with an
+ * solves use rel_tol 1e-10, preconditioner `precond` and FGMRES(m) with m from
+ * mmc_set_solve_params (default 48), with an
  * FP32 inner solve, or FP64 throughout when prec = MMC_F64.
  * samples_out (2 n_noise doubles, may be NULL) receives the samples. */
 int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int n_noise,
@@ -281,6 +295,10 @@ typedef struct {
 int mmc_profile(mmc_ctx* ctx, int enable);
 /* Synchronise the context's work and read the counters. */
 int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out);
+
+/* Inner FGMRES length and outer-cycle limit of the solves inside mmc_trace_level
+ * (defaults 48 and 400).  Values <= 0 keep the current setting. */
+int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
 
 /* Launch variant of the fused step kernel for precision prec: rpt right-hand
  * sides per lane (1, 2; F64 uses 1), minb = minimum resident CTAs per SM asked

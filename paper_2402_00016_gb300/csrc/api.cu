@@ -67,7 +67,10 @@ int mmc_destroy(mmc_ctx* ctx) {
   if (ctx->U) cudaFree(ctx->U);
   if (ctx->Z32) cudaFree(ctx->Z32);
   if (ctx->U32) cudaFree(ctx->U32);
+  for (auto b : ctx->tcB)
+    if (b) cudaFree(b);
   prof_collect(ctx);
+  for (auto& kv : ctx->coef_cache) cudaFree(kv.second.p);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -172,6 +175,13 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out) {
   return MMC_OK;
 }
 
+int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer) {
+  if (!ctx) return MMC_ERR_ARG;
+  if (m_inner > 0) ctx->solve_m = m_inner;
+  if (max_outer > 0) ctx->solve_max_outer = max_outer;
+  return MMC_OK;
+}
+
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
   if (!ctx || prec < 0 || prec > 2) return MMC_ERR_ARG;
   if (minb >= 100) {  // minb = 100 + v selects kernel version v (1: generic, 2: compile-time rhs block)
@@ -209,6 +219,7 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   CK(cudaEventCreate(&e1));
   const int rpts[2] = {1, 2};
   const int minbs[3] = {1, 3, 4};
+  const int minbs2[2] = {4, 6};  // v2, one rhs per lane: 128 or 80 registers
   const int spcs[4] = {32, 64, 128, 256};
   double best_ms = 1e300;
   int br = ctx->var_rpt[prec], bm = ctx->var_minb[prec], bs = ctx->spc_step, bv = ctx->var_ver[prec];
@@ -217,11 +228,13 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   for (int ri = 0; ri < 2; ++ri) {
     if (prec == MMC_F64 && rpts[ri] != 1) continue;
     if (rpts[ri] > g.R) continue;
-    for (int mi = 0; mi < (ver == 2 ? 1 : 3); ++mi) {  // the v2 kernel fixes its register cap per rpt
+    const int nmb = ver == 1 ? 3 : (rpts[ri] == 1 ? 2 : 1);  // v2 with two rhs per lane has one cap
+    for (int mi = 0; mi < nmb; ++mi) {
+      const int mbv = ver == 1 ? minbs[mi] : (rpts[ri] == 1 ? minbs2[mi] : 3);
       for (int si = 0; si < 4; ++si) {
         ctx->var_ver[prec] = ver;
         ctx->var_rpt[prec] = rpts[ri];
-        ctx->var_minb[prec] = minbs[mi];
+        ctx->var_minb[prec] = mbv;
         ctx->spc_step = spcs[si];
         TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
         std::vector<float> t;
@@ -238,7 +251,7 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
         if (t[1] < best_ms) {
           best_ms = t[1];
           br = rpts[ri];
-          bm = minbs[mi];
+          bm = mbv;
           bs = spcs[si];
           bv = ver;
         }

@@ -204,7 +204,10 @@ __device__ __forceinline__ void theta_dot(const double2 (&a)[12], const double2 
   }
 }
 
-template <typename T>
+// partial[bx][i][npad] = sum over the CTA's sites of conj(A_i) . Theta w, for i < nvec.
+// Basis vectors are processed NB at a time: w is read once per chunk and the NB
+// sums stay in registers (FP32 for FP32/BF16 fields, FP64 for FP64 fields).
+template <typename T, int NB>
 __global__ void multidot_kernel(geom g, const T* A, size_t a_stride, int nvec, const T* w, int theta, int spc,
                                 double2* partial) {
   using R = typename Arith<T>::R;
@@ -214,25 +217,37 @@ __global__ void multidot_kernel(geom g, const T* A, size_t a_stride, int nvec, c
   const int r = threadIdx.x % g.R;
   const int spp = blockDim.x / g.R;
   const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
-  for (int i = 0; i < nvec; ++i) {
-    R re = 0, im = 0;
+  for (int i0 = 0; i0 < nvec; i0 += NB) {
+    R re[NB], im[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) re[q] = im[q] = R(0);
     for (int s0 = s_begin; s0 < s_end; s0 += spp) {
-      int site = s0 + threadIdx.x / g.R;
+      const int site = s0 + threadIdx.x / g.R;
       if (site >= s_end) continue;
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
         const int src = (theta == 1) ? (c + 6) % 12 : c;
         const R sg = (theta == 2 && c >= 6) ? R(-1) : R(1);
-        C a = getc<T>(A + size_t(i) * a_stride, fidx(g, rb, site, c, r));
-        C x = getc<T>(w, fidx(g, rb, site, src, r));
-        re += sg * (a.x * x.x + a.y * x.y);
-        im += sg * (a.x * x.y - a.y * x.x);
+        const C x = getc<T>(w, fidx(g, rb, site, src, r));
+        const size_t e = fidx(g, rb, site, c, r);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          if (i0 + q < nvec) {
+            const C a = getc<T>(A + size_t(i0 + q) * a_stride, e);
+            re[q] += sg * (a.x * x.x + a.y * x.y);
+            im[q] += sg * (a.x * x.y - a.y * x.x);
+          }
+        }
       }
     }
-    double dre = re, dim = im;
-    cta_reduce_r(dre, dim, g.R, sh);
-    if (threadIdx.x < g.R)
-      partial[(size_t(blockIdx.x) * nvec + i) * g.npad + rb * g.R + threadIdx.x] = make_double2(dre, dim);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      if (i0 + q >= nvec) break;
+      double dre = re[q], dim = im[q];
+      cta_reduce_r(dre, dim, g.R, sh);
+      if (threadIdx.x < g.R)
+        partial[(size_t(blockIdx.x) * nvec + i0 + q) * g.npad + rb * g.R + threadIdx.x] = make_double2(dre, dim);
+    }
   }
 }
 
@@ -556,11 +571,11 @@ cudaError_t launch_multidot(int prec, geom g, const void* A, size_t a_stride, in
                             int spc, double2* partial, cudaStream_t s) {
   dim3 grid((g.V + spc - 1) / spc, g.nrb);
   if (prec == 0)
-    multidot_kernel<double2><<<grid, 256, 0, s>>>(g, (const double2*)A, a_stride, nvec, (const double2*)w, theta,
-                                                  spc, partial);
+    multidot_kernel<double2, 4><<<grid, 256, 0, s>>>(g, (const double2*)A, a_stride, nvec, (const double2*)w, theta,
+                                                     spc, partial);
   else
-    multidot_kernel<float2><<<grid, 256, 0, s>>>(g, (const float2*)A, a_stride, nvec, (const float2*)w, theta, spc,
-                                                 partial);
+    multidot_kernel<float2, 8><<<grid, 256, 0, s>>>(g, (const float2*)A, a_stride, nvec, (const float2*)w, theta,
+                                                    spc, partial);
   count_launch();
   return cudaGetLastError();
 }

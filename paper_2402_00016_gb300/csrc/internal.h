@@ -64,7 +64,17 @@ struct mmc_ctx {
   double2* U = nullptr;
   float2* Z32 = nullptr;  // FP32 copies used by the FP32 / BF16 levels (projections and correction alike)
   float2* U32 = nullptr;
+  // BF16 copies [Theta z; u] for the tensor-core projections of BF16 levels, per Theta
+  void* tcB[3] = {nullptr, nullptr, nullptr};
+  bool use_tc = true;
   std::map<std::string, mmc::host::DevBuf> scratch;
+  // device copies of step coefficient tables, keyed by a hash of their contents:
+  // a polynomial applied again (preconditioner, chains of later steps) reuses its
+  // table without a host-to-device copy or a stream synchronisation
+  std::map<uint64_t, mmc::host::DevBuf> coef_cache;
+  size_t coef_cache_bytes = 0;
+  int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
+  int solve_max_outer = 400;
   std::string err;
   long long matvecs = 0;
   int spc_step = 64;  // sites per CTA of the step kernel (all precisions: partial buffers depend on it)
@@ -215,9 +225,33 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
   for (size_t k = 0; k < run.steps.size(); ++k)
     for (size_t i = 0; i < per; ++i)
       host[k * per + i] = make_double2(run.steps[k].coef[i].real(), run.steps[k].coef[i].imag());
-  void* dcoef;
-  TRY(scratch(ctx, "coef", host.size() * sizeof(double2), &dcoef));
-  CK(cudaMemcpyAsync(dcoef, host.data(), host.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  // FNV-1a hash of the table (and its size) as the cache key
+  uint64_t key = 1469598103934665603ull ^ host.size();
+  {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(host.data());
+    const size_t nb = host.size() * sizeof(double2);
+    for (size_t i = 0; i < nb; ++i) key = (key ^ b[i]) * 1099511628211ull;
+  }
+  void* dcoef = nullptr;
+  auto hit = ctx->coef_cache.find(key);
+  if (hit != ctx->coef_cache.end() && hit->second.bytes == host.size() * sizeof(double2)) {
+    dcoef = hit->second.p;
+  } else {
+    const size_t nb = host.size() * sizeof(double2);
+    if (ctx->coef_cache_bytes + nb > (size_t(256) << 20)) {  // bounded: drop the whole cache
+      CK(cudaStreamSynchronize(s));
+      for (auto& kv : ctx->coef_cache) cudaFree(kv.second.p);
+      ctx->coef_cache.clear();
+      ctx->coef_cache_bytes = 0;
+    }
+    DevBuf b;
+    CK(cudaMalloc(&b.p, nb));
+    b.bytes = nb;
+    CK(cudaMemcpyAsync(b.p, host.data(), nb, cudaMemcpyHostToDevice, s));
+    ctx->coef_cache[key] = b;
+    ctx->coef_cache_bytes += nb;
+    dcoef = b.p;
+  }
   const int rpt = rpt_for(ctx, run.prec, g.R);
   for (size_t k = 0; k < run.steps.size(); ++k) {
     const Step& st = run.steps[k];
@@ -256,15 +290,16 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     bool done = false;
     if (ctx->var_ver[run.prec] == 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
       cudaError_t e2 = cudaSuccess;
-      done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, p, g.nrb, s, &e2)
-                                 : mmc::launch_step2_bf16(g.R, rpt, p, g.nrb, s, &e2);
+      const int mb = ctx->var_minb[run.prec];
+      done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, mb, p, g.nrb, s, &e2)
+                                 : mmc::launch_step2_bf16(g.R, rpt, mb, p, g.nrb, s, &e2);
       CK(e2);
     }
     if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec], p, g.nrb, s));
     if (ctx->prof) {
       CK(cudaEventRecord(e1, s));
       ctx->ev_pending.push_back({e0, e1});
-      if (ctx->ev_pending.size() > 4096) TRY(prof_collect(ctx));
+      if (ctx->ev_pending.size() > 65536) TRY(prof_collect(ctx));
       ctx->prof_launches += 1;
       // algorithmic bytes and flops of this launch (all rhs blocks active)
       const double sb = double(elem_bytes(run.prec)) * 12;  // one spinor, one rhs
@@ -331,6 +366,38 @@ inline void build_single(const mmc_ctx* ctx, Run& run, const std::vector<cd>& th
     cd it = 1.0 / th[k];
     cd wo = (k == m - 2) ? scale / th[m - 1] : cd(0, 0);
     for (int r = 0; r < nrhs; ++r) set_coef(st.coef, npad, r, 1.0 - it, kap * it, 0, scale * it, wo);
+    run.steps.push_back(st);
+  }
+}
+
+// Steps of p(M) x in Horner nesting, p(M) x = c_1 x + (1 - M/t_1)(c_2 x + (1 - M/t_2)(... c_m x)),
+// c_k = 1/t_k: the same polynomial as the sum of u_k (Sec. 3) with no accumulator field;
+// each step reads the iterate (neighbours) and x (site-local) and writes the next iterate.
+// Used where any fixed evaluation of p will do (the FGMRES preconditioner).  m >= 2.
+inline void build_horner(const mmc_ctx* ctx, Run& run, const std::vector<cd>& th, const void* x, void* P0, void* P1,
+                         void* out, int nrhs) {
+  const int m = int(th.size());
+  const int npad = run.g.npad;
+  const double kap = ctx->kappa;
+  void* P[2] = {P0, P1};
+  int n = 0;
+  for (int k = m - 2; k >= 0; --k, ++n) {
+    Step st;
+    st.coef = coef_block(npad);
+    const cd ck = 1.0 / th[k], it = 1.0 / th[k];
+    st.out = (k == 0) ? out : P[n & 1];
+    st.flags = mmc::SF_HOP | mmc::SF_WRITE;
+    if (k == m - 2) {
+      // w = c_{m-1} x folded in: out = [c_{m-1}(1 - 1/t_k) + c_k] x + c_{m-1} (kappa/t_k) D x
+      const cd cm = 1.0 / th[m - 1];
+      st.in = x;
+      for (int r = 0; r < nrhs; ++r) set_coef(st.coef, npad, r, cm * (1.0 - it) + ck, cm * kap * it, 0, 0, 0);
+    } else {
+      st.in = P[(n - 1) & 1];
+      st.aux = x;
+      st.flags |= mmc::SF_AUX;
+      for (int r = 0; r < nrhs; ++r) set_coef(st.coef, npad, r, 1.0 - it, kap * it, ck, 0, 0);
+    }
     run.steps.push_back(st);
   }
 }

@@ -22,8 +22,9 @@ cudaError_t launch_step(int prec, int rpt, int minb, const step_params& p, int n
 
 // Step kernel v2 (stencil2_*.cu): compile-time rhs block R (8 or 16) and epilogue
 // mode; returns false (nothing launched) when the flags or R need step_kernel.
-bool launch_step2_f32(int R, int rpt, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
-bool launch_step2_bf16(int R, int rpt, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
+// minb (RPT = 1 only): 6 caps registers at 80 (24 warps per SM), else 128 (16 warps).
+bool launch_step2_f32(int R, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
+bool launch_step2_bf16(int R, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
 
 // Z(4) noise (Sec. 1) into a field of precision prec and/or packed codes.
 // ids[r] = (level, noise index) for rhs r (npad entries, device); entries with
@@ -91,6 +92,16 @@ cudaError_t launch_net_layer(const net_geom& g, int ci, int co, const float2* in
 // partial[b][9][co][ci] over b = rb * nbx + bx: sum delta conj(feature) (weight gradients).
 cudaError_t launch_net_wgrad(const net_geom& g, int ci, int co, const float2* in, const float2* delta, int spc,
                              double2* partial, cudaStream_t s);
+
+// Tensor-core deflation projections (tc_proj.cu): BF16 copy of [Theta z; u] (256 x Kp),
+// the correction dots from that copy, and the projections P (FP64, rows 2 npad padded
+// to 128, 256 columns) of a noise batch.
+size_t tc_proj_smem_bytes();
+cudaError_t launch_tc_pack_eig(int V, int k, long long Kp, int theta, const float2* Z, const float2* U, void* B,
+                               cudaStream_t s);
+cudaError_t launch_tc_pair_dots(long long Kp, int k, const void* B, double2* d, cudaStream_t s);
+cudaError_t launch_tc_proj(const geom& g, const uint32_t* codes, const void* B, long long Kp, int nsplit,
+                           float* partial, double* P, int* err, cudaStream_t s);
 
 // Complex small-matrix kernels on the device for the Arnoldi bookkeeping.
 // hcol[i] = h1[i] + h2[i] for i < n (per rhs), written into H column storage.

@@ -136,6 +136,26 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
         if (is_net(ctx, precond)) {
           if (ip != MMC_F32) RET(MMC_ERR_ARG, "mmc_solve: the learned preconditioner needs an FP32 inner solve");
           TRY(net_apply(ctx, precond, vj, zdst, g.npad, s, nullptr));
+        } else if (ctx->polys[precond].kind == 0 && ctx->polys[precond].op == MMC_OP_M &&
+                   ctx->polys[precond].theta.size() >= 2) {
+          // single polynomial: Horner nesting, no accumulator field (3 field passes per degree)
+          const int hp = prec_inner == MMC_BF16 ? MMC_BF16 : ip;
+          void *Q0, *Q1, *src = const_cast<void*>(vj), *dst = zdst;
+          TRY(scratch(ctx, "sv_h0", field_bytes(g, hp), &Q0));
+          TRY(scratch(ctx, "sv_h1", field_bytes(g, hp), &Q1));
+          if (hp != ip) {
+            void* v16;
+            void* o16;
+            TRY(scratch(ctx, "sv_v16", field_bytes(g, hp), &v16));
+            TRY(scratch(ctx, "sv_o16", field_bytes(g, hp), &o16));
+            CK(mmc::launch_convert(hp, v16, ip, vj, g, s));
+            src = v16;
+            dst = o16;
+          }
+          base.prec = hp;
+          build_horner(ctx, base, ctx->polys[precond].theta, src, Q0, Q1, dst, g.npad);
+          TRY(exec_run(ctx, base, s));
+          if (hp != ip) CK(mmc::launch_convert(ip, zdst, hp, dst, g, s));
         } else if (prec_inner == MMC_BF16) {
           void* v16;
           TRY(scratch(ctx, "sv_v16", field_bytes(g, MMC_BF16), &v16));
@@ -388,6 +408,10 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
   if (ctx->U32) cudaFree(ctx->U32);
   ctx->Z = ctx->U = nullptr;
   ctx->Z32 = ctx->U32 = nullptr;
+  for (auto& b : ctx->tcB) {
+    if (b) cudaFree(b);
+    b = nullptr;
+  }
   ctx->k_defl = 0;
   ctx->lambda.clear();
   if (kk > 0) {
@@ -440,6 +464,72 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
       lambda_out[2 * i] = ctx->lambda[i].real();
       lambda_out[2 * i + 1] = ctx->lambda[i].imag();
     }
+  return MMC_OK;
+}
+
+int mmc_set_deflation(mmc_ctx* ctx, int k, const double* lambda, const double* Z, const double* U) {
+  TRY(check_ctx(ctx));
+  if (k < 0 || (k > 0 && (!lambda || !Z || !U))) RET(MMC_ERR_ARG, "mmc_set_deflation: bad argument");
+  cudaStream_t s = ctx->stream;
+  if (ctx->Z) cudaFree(ctx->Z);
+  if (ctx->U) cudaFree(ctx->U);
+  if (ctx->Z32) cudaFree(ctx->Z32);
+  if (ctx->U32) cudaFree(ctx->U32);
+  ctx->Z = ctx->U = nullptr;
+  ctx->Z32 = ctx->U32 = nullptr;
+  for (auto& b : ctx->tcB) {
+    if (b) cudaFree(b);
+    b = nullptr;
+  }
+  ctx->k_defl = 0;
+  ctx->lambda.clear();
+  if (k == 0) return MMC_OK;
+  const geom g1 = make_geom(ctx, 1);
+  const size_t fb = field_bytes(g1, MMC_F64);
+  const size_t n = size_t(ctx->V) * 12;
+  CK(cudaMalloc(&ctx->Z, fb * k));
+  CK(cudaMalloc(&ctx->U, fb * k));
+  void* canon;
+  TRY(scratch(ctx, "canon", fb, &canon));
+  for (int i = 0; i < k; ++i) {  // canonical host order -> device single-vector layout ([site][12] either way)
+    CK(cudaMemcpy(canon, Z + 2 * n * i, fb, cudaMemcpyHostToDevice));
+    CK(mmc::launch_pack(MMC_F64, g1, 1, (const double2*)canon, ctx->Z + n * i, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(canon, U + 2 * n * i, fb, cudaMemcpyHostToDevice));
+    CK(mmc::launch_pack(MMC_F64, g1, 1, (const double2*)canon, ctx->U + n * i, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaMalloc(&ctx->Z32, fb / 2 * k));
+  CK(cudaMalloc(&ctx->U32, fb / 2 * k));
+  const geom gk = {ctx->V * k, 1, 1, 1};
+  CK(mmc::launch_convert(MMC_F32, ctx->Z32, MMC_F64, ctx->Z, gk, s));
+  CK(mmc::launch_convert(MMC_F32, ctx->U32, MMC_F64, ctx->U, gk, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < k; ++i) ctx->lambda.push_back(cd(lambda[2 * i], lambda[2 * i + 1]));
+  ctx->k_defl = k;
+  return MMC_OK;
+}
+
+int mmc_get_deflation(mmc_ctx* ctx, int* k, double* lambda, double* Z, double* U) {
+  if (!ctx || !k) return MMC_ERR_ARG;
+  *k = ctx->k_defl;
+  if (!lambda && !Z && !U) return MMC_OK;
+  CK(cudaSetDevice(ctx->device));
+  const size_t n = size_t(ctx->V) * 12;
+  for (int i = 0; i < ctx->k_defl; ++i) {
+    if (lambda) {
+      lambda[2 * i] = ctx->lambda[i].real();
+      lambda[2 * i + 1] = ctx->lambda[i].imag();
+    }
+    if (Z) CK(cudaMemcpy(Z + 2 * n * i, ctx->Z + n * i, n * sizeof(double2), cudaMemcpyDeviceToHost));
+    if (U) CK(cudaMemcpy(U + 2 * n * i, ctx->U + n * i, n * sizeof(double2), cudaMemcpyDeviceToHost));
+  }
+  return MMC_OK;
+}
+
+int mmc_set_tensor_projections(mmc_ctx* ctx, int enable) {
+  if (!ctx) return MMC_ERR_ARG;
+  ctx->use_tc = enable != 0;
   return MMC_OK;
 }
 
@@ -523,8 +613,8 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     std::vector<double> rel;
     int its = 0;
     // the plain FP64 form (prec = MMC_F64) solves in FP64 throughout; otherwise FP32 inner
-    TRY(solve_impl(ctx, b64, x64, n_noise, 1e-10, precond, prec == MMC_F64 ? MMC_F64 : MMC_F32, 48, 400, &its, rel,
-                   s));
+    TRY(solve_impl(ctx, b64, x64, n_noise, 1e-10, precond, prec == MMC_F64 ? MMC_F64 : MMC_F32, ctx->solve_m,
+                   ctx->solve_max_outer, &its, rel, s));
     const int nb2 = (g.V + kSpc - 1) / kSpc;
     CK(cudaMemsetAsync(part, 0, size_t(nb2) * g.npad * sizeof(double2), s));
     CK(mmc::launch_bilinear_codes(MMC_F64, g, (const uint32_t*)codes, theta_op, x64, kSpc, (double2*)part, s));
@@ -545,23 +635,68 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     void *pa, *pb;
     TRY(scratch(ctx, "lv_pa", size_t(nb2) * k * g.npad * sizeof(double2), &pa));
     TRY(scratch(ctx, "lv_pb", size_t(nb2) * k * g.npad * sizeof(double2), &pb));
-    const int dp = prec == MMC_F64 ? MMC_F64 : MMC_F32;  // eigenvector copy matching the level's precision
-    const void* Zd = dp == MMC_F64 ? (const void*)ctx->Z : (const void*)ctx->Z32;
-    const void* Ud = dp == MMC_F64 ? (const void*)ctx->U : (const void*)ctx->U32;
-    CK(mmc::launch_defl_proj(dp, g, (const uint32_t*)codes, theta_op, Zd, Ud, k, kSpc, (double2*)pa, (double2*)pb, s));
-    std::vector<cd> A, B;
-    TRY(reduce_to_host(ctx, (double2*)pa, nb2, k, g.npad, A, s));
-    TRY(reduce_to_host(ctx, (double2*)pb, nb2, k, g.npad, B, s));
     const size_t n = size_t(ctx->V) * 12;
+    std::vector<cd> A, B, D(k);
+    if (prec != MMC_F64 && ctx->use_tc && k <= 128) {
+      // tensor cores: one BF16 GEMM for both projections; the correction from the same BF16 copy
+      const long long Kp = ((24ll * ctx->V + 63) / 64) * 64;
+      if (!ctx->tcB[theta_op]) {
+        CK(cudaMalloc(&ctx->tcB[theta_op], size_t(256) * Kp * 2));
+        CK(mmc::launch_tc_pack_eig(ctx->V, k, Kp, theta_op, ctx->Z32, ctx->U32, ctx->tcB[theta_op], s));
+      }
+      const int mtiles = (2 * g.npad + 127) / 128;
+      int nsplit = std::max(1, 148 / mtiles);
+      nsplit = int(std::min<long long>(nsplit, Kp / 64));
+      void *tpart, *tP, *terr, *tdots;
+      TRY(scratch(ctx, "tc_part", size_t(nsplit) * mtiles * 128 * 256 * sizeof(float), &tpart));
+      TRY(scratch(ctx, "tc_P", size_t(mtiles) * 128 * 256 * sizeof(double), &tP));
+      TRY(scratch(ctx, "tc_err", sizeof(int), &terr));
+      TRY(scratch(ctx, "tc_dots", size_t(k) * sizeof(double2), &tdots));
+      CK(cudaMemsetAsync(terr, 0, sizeof(int), s));
+      CK(mmc::launch_tc_proj(g, (const uint32_t*)codes, ctx->tcB[theta_op], Kp, nsplit, (float*)tpart, (double*)tP,
+                             (int*)terr, s));
+      CK(mmc::launch_tc_pair_dots(Kp, k, ctx->tcB[theta_op], (double2*)tdots, s));
+      std::vector<double> P(size_t(mtiles) * 128 * 256);
+      std::vector<double2> dd(k);
+      int herr = 0;
+      CK(cudaMemcpyAsync(P.data(), tP, P.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(dd.data(), tdots, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (herr) RET(MMC_ERR_TIMEOUT, "mmc_trace_level: tensor-core projection wait timed out");
+      A.assign(size_t(k) * g.npad, cd(0, 0));
+      B.assign(size_t(k) * g.npad, cd(0, 0));
+      for (int i = 0; i < k; ++i)
+        for (int r = 0; r < g.npad; ++r) {
+          const double* row0 = &P[size_t(2 * r) * 256];
+          const double* row1 = &P[size_t(2 * r + 1) * 256];
+          A[size_t(i) * g.npad + r] = cd(row0[i], -row1[i]);
+          B[size_t(i) * g.npad + r] = cd(row0[128 + i], row1[128 + i]);
+        }
+      for (int i = 0; i < k; ++i) D[i] = cd(dd[i].x, dd[i].y);
+    } else {
+      const int dp = prec == MMC_F64 ? MMC_F64 : MMC_F32;  // eigenvector copy matching the level's precision
+      const void* Zd = dp == MMC_F64 ? (const void*)ctx->Z : (const void*)ctx->Z32;
+      const void* Ud = dp == MMC_F64 ? (const void*)ctx->U : (const void*)ctx->U32;
+      CK(mmc::launch_defl_proj(dp, g, (const uint32_t*)codes, theta_op, Zd, Ud, k, kSpc, (double2*)pa, (double2*)pb,
+                               s));
+      TRY(reduce_to_host(ctx, (double2*)pa, nb2, k, g.npad, A, s));
+      TRY(reduce_to_host(ctx, (double2*)pb, nb2, k, g.npad, B, s));
+      for (int i = 0; i < k; ++i) {
+        const void* ui =
+            dp == MMC_F64 ? (const void*)(ctx->U + size_t(i) * n) : (const void*)(ctx->U32 + size_t(i) * n);
+        const void* zi =
+            dp == MMC_F64 ? (const void*)(ctx->Z + size_t(i) * n) : (const void*)(ctx->Z32 + size_t(i) * n);
+        CK(mmc::launch_multidot(dp, g1, ui, 0, 1, zi, theta_op, kSpc, (double2*)part, s));
+        std::vector<cd> d;
+        TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, 1, d, s));
+        D[i] = d[0];
+      }
+    }
     for (int i = 0; i < k; ++i) {
       cd c = poly_value(ctx, hi, ctx->lambda[i]) - (lo == MMC_ZERO ? cd(0, 0) : poly_value(ctx, lo, ctx->lambda[i]));
       for (int r = 0; r < n_noise; ++r) x[r] -= c * A[size_t(i) * g.npad + r] * B[size_t(i) * g.npad + r];
-      const void* ui = dp == MMC_F64 ? (const void*)(ctx->U + size_t(i) * n) : (const void*)(ctx->U32 + size_t(i) * n);
-      const void* zi = dp == MMC_F64 ? (const void*)(ctx->Z + size_t(i) * n) : (const void*)(ctx->Z32 + size_t(i) * n);
-      CK(mmc::launch_multidot(dp, g1, ui, 0, 1, zi, theta_op, kSpc, (double2*)part, s));
-      std::vector<cd> d;
-      TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, 1, d, s));
-      corr += c * d[0];
+      corr += c * D[i];
     }
   }
   // statistics (Sec. 4, Sec. 8 readings: unbiased variance of each part, stderr = s / sqrt(N))

@@ -13,9 +13,10 @@ using namespace sten;
 
 enum Acc { ACC_NONE = 0, ACC_CODES = 1, ACC_Y = 2, ACC_LEFT = 3 };
 
-// RPT = 2 is capped at 168 registers (3 CTAs of 128 threads per SM), RPT = 1 at 128 (4 CTAs).
-template <typename S, int R, int RPT, int KD, bool AUX, int ACC>
-__global__ void __launch_bounds__(128, RPT == 1 ? 4 : 3) step2_kernel(step_params p) {
+// MINB resident CTAs of 128 threads per SM cap the registers: RPT = 2 uses 3 (168
+// registers), RPT = 1 uses 4 (128) or 6 (80, more warps to hide memory latency).
+template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC>
+__global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
   using T = float;
   constexpr int L = R / RPT;      // lanes per site
   constexpr int SPP = 128 / L;    // sites per pass of the CTA
@@ -119,20 +120,29 @@ __global__ void __launch_bounds__(128, RPT == 1 ? 4 : 3) step2_kernel(step_param
       if (BIL) {
         const int cp = (p.theta == 1) ? (c + 6) % 12 : c;
         const T sg = (p.theta == 2 && c >= 6) ? T(-1) : T(1);
-        cx<T> eta[RPT];
         if (ACC == ACC_CODES) {
+          // conj(i^k) v is v turned by -k quarter turns: k odd swaps (re, im) -> (im, -re),
+          // k >= 2 negates; the gamma_5 sign folds into the same factor
 #pragma unroll
           for (int j = 0; j < RPT; ++j) {
             const uint32_t k = (code[j] >> (2 * cp)) & 3u;
-            eta[j] = cmake(k == 0 ? T(1) : (k == 2 ? T(-1) : T(0)), k == 1 ? T(1) : (k == 3 ? T(-1) : T(0)));
+            const T f = (k & 2u) ? -sg : sg;
+            const bool odd = (k & 1u) != 0;
+            si[j].re = fmaf(f, odd ? vin[j].im : vin[j].re, si[j].re);
+            si[j].im = fmaf(f, odd ? -vin[j].re : vin[j].im, si[j].im);
+            if (bil_out) {
+              so[j].re = fmaf(f, odd ? vout[j].im : vout[j].re, so[j].re);
+              so[j].im = fmaf(f, odd ? -vout[j].re : vout[j].im, so[j].im);
+            }
           }
         } else {
+          cx<T> eta[RPT];
           load_rpt<S, RPT>(reinterpret_cast<const S*>(p.left) + boff + size_t(cp) * R, eta);
-        }
 #pragma unroll
-        for (int j = 0; j < RPT; ++j) {
-          si[j] = cfmac(eta[j], cscale(vin[j], sg), si[j]);
-          if (bil_out) so[j] = cfmac(eta[j], cscale(vout[j], sg), so[j]);
+          for (int j = 0; j < RPT; ++j) {
+            si[j] = cfmac(eta[j], cscale(vin[j], sg), si[j]);
+            if (bil_out) so[j] = cfmac(eta[j], cscale(vout[j], sg), so[j]);
+          }
         }
       }
     }
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(128, RPT == 1 ? 4 : 3) step2_kernel(step_param
 
 // Dispatch of one (S, R, RPT) family over the epilogue modes; returns false when
 // the flags need the generic kernel.
-template <typename S, int R, int RPT>
+template <typename S, int R, int RPT, int MINB>
 bool launch2(const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err) {
   const int f = p.flags;
   if (!(f & SF_HOP) || !(f & SF_WRITE)) return false;
@@ -193,20 +203,20 @@ bool launch2(const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err) {
   dim3 grid((p.V + p.spc - 1) / p.spc, n_rb);
   if (f & SF_DAGGER) {
     if (aux || acc != ACC_NONE) return false;
-    step2_kernel<S, R, RPT, -1, false, ACC_NONE><<<grid, 128, 0, s>>>(p);
+    step2_kernel<S, R, RPT, MINB, -1, false, ACC_NONE><<<grid, 128, 0, s>>>(p);
   } else if (!aux) {
     switch (acc) {
-      case ACC_NONE: step2_kernel<S, R, RPT, 1, false, ACC_NONE><<<grid, 128, 0, s>>>(p); break;
-      case ACC_CODES: step2_kernel<S, R, RPT, 1, false, ACC_CODES><<<grid, 128, 0, s>>>(p); break;
-      case ACC_Y: step2_kernel<S, R, RPT, 1, false, ACC_Y><<<grid, 128, 0, s>>>(p); break;
-      default: step2_kernel<S, R, RPT, 1, false, ACC_LEFT><<<grid, 128, 0, s>>>(p); break;
+      case ACC_NONE: step2_kernel<S, R, RPT, MINB, 1, false, ACC_NONE><<<grid, 128, 0, s>>>(p); break;
+      case ACC_CODES: step2_kernel<S, R, RPT, MINB, 1, false, ACC_CODES><<<grid, 128, 0, s>>>(p); break;
+      case ACC_Y: step2_kernel<S, R, RPT, MINB, 1, false, ACC_Y><<<grid, 128, 0, s>>>(p); break;
+      default: step2_kernel<S, R, RPT, MINB, 1, false, ACC_LEFT><<<grid, 128, 0, s>>>(p); break;
     }
   } else {
     switch (acc) {
-      case ACC_NONE: step2_kernel<S, R, RPT, 1, true, ACC_NONE><<<grid, 128, 0, s>>>(p); break;
-      case ACC_CODES: step2_kernel<S, R, RPT, 1, true, ACC_CODES><<<grid, 128, 0, s>>>(p); break;
-      case ACC_Y: step2_kernel<S, R, RPT, 1, true, ACC_Y><<<grid, 128, 0, s>>>(p); break;
-      default: step2_kernel<S, R, RPT, 1, true, ACC_LEFT><<<grid, 128, 0, s>>>(p); break;
+      case ACC_NONE: step2_kernel<S, R, RPT, MINB, 1, true, ACC_NONE><<<grid, 128, 0, s>>>(p); break;
+      case ACC_CODES: step2_kernel<S, R, RPT, MINB, 1, true, ACC_CODES><<<grid, 128, 0, s>>>(p); break;
+      case ACC_Y: step2_kernel<S, R, RPT, MINB, 1, true, ACC_Y><<<grid, 128, 0, s>>>(p); break;
+      default: step2_kernel<S, R, RPT, MINB, 1, true, ACC_LEFT><<<grid, 128, 0, s>>>(p); break;
     }
   }
   count_launch();

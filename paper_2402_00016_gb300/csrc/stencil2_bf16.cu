@@ -2,9 +2,15 @@
 #include "stencil2.cuh"
 
 namespace mmc {
-bool launch_step2_bf16(int R, int rpt, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err) {
-  if (R == 16) return rpt == 1 ? sten2::launch2<__nv_bfloat162, 16, 1>(p, n_rb, s, err) : sten2::launch2<__nv_bfloat162, 16, 2>(p, n_rb, s, err);
-  if (R == 8) return rpt == 1 ? sten2::launch2<__nv_bfloat162, 8, 1>(p, n_rb, s, err) : sten2::launch2<__nv_bfloat162, 8, 2>(p, n_rb, s, err);
+bool launch_step2_bf16(int R, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err) {
+  if (R == 16) {
+    if (rpt == 2) return sten2::launch2<__nv_bfloat162, 16, 2, 3>(p, n_rb, s, err);
+    return minb >= 6 ? sten2::launch2<__nv_bfloat162, 16, 1, 6>(p, n_rb, s, err) : sten2::launch2<__nv_bfloat162, 16, 1, 4>(p, n_rb, s, err);
+  }
+  if (R == 8) {
+    if (rpt == 2) return sten2::launch2<__nv_bfloat162, 8, 2, 3>(p, n_rb, s, err);
+    return minb >= 6 ? sten2::launch2<__nv_bfloat162, 8, 1, 6>(p, n_rb, s, err) : sten2::launch2<__nv_bfloat162, 8, 1, 4>(p, n_rb, s, err);
+  }
   return false;
 }
 }  // namespace mmc

@@ -79,6 +79,9 @@ _SIGS = {
     "mmc_apply_poly": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
     "mmc_deflate": (_i, [_vp, _i, _i, _i, _d, _dp, _ip]),
     "mmc_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _i, _ip, _dp]),
+    "mmc_set_deflation": (_i, [_vp, _i, _dp, _dp, _dp]),
+    "mmc_get_deflation": (_i, [_vp, _ip, _dp, _dp, _dp]),
+    "mmc_set_tensor_projections": (_i, [_vp, _i]),
     "mmc_trace_level": (_i, [_vp, _i, _i, _i, _i, _i, _u32, _u32, _i, _i,
                              ctypes.POINTER(mmc_level_stats), _dp]),
     "mmc_trace_exact": (_i, [_vp, _i, _i, _i, _i, _dp]),
@@ -93,6 +96,7 @@ _SIGS = {
     "mmc_profile_read": (_i, [_vp, ctypes.POINTER(mmc_profile_stats)]),
     "mmc_update_gauge": (_i, [_vp, _dp]),
     "mmc_set_step_variant": (_i, [_vp, _i, _i, _i, _i]),
+    "mmc_set_solve_params": (_i, [_vp, _i, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
     "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
     "mmc_leja_order": (_i, [_i, _dp, _dp]),
@@ -245,6 +249,30 @@ def mmc_deflate(ctx, k, poly_handle, m_arnoldi, tol_accept=1e-3):
     return (lam[0::2] + 1j * lam[1::2])[: ka.value]
 
 
+def mmc_set_deflation(ctx, lam, Z, U):
+    """Z, U: arrays (k, 12V) complex in canonical order; lam: k complex."""
+    lam, pl = _cplx(np.atleast_1d(lam))
+    Z, pz = _cplx(Z)
+    U, pu = _cplx(U)
+    _check(lib.mmc_set_deflation(ctx, int(lam.size), pl, pz, pu), ctx)
+
+
+def mmc_get_deflation(ctx, vol):
+    k = ctypes.c_int()
+    _check(lib.mmc_get_deflation(ctx, ctypes.byref(k), None, None, None), ctx)
+    lam = np.zeros(2 * k.value)
+    Z = np.zeros(2 * k.value * 12 * int(vol))
+    U = np.zeros(2 * k.value * 12 * int(vol))
+    _check(lib.mmc_get_deflation(ctx, ctypes.byref(k), lam.ctypes.data_as(_dp), Z.ctypes.data_as(_dp),
+                                 U.ctypes.data_as(_dp)), ctx)
+    c = lambda a: (a[0::2] + 1j * a[1::2])
+    return c(lam), c(Z).reshape(k.value, -1), c(U).reshape(k.value, -1)
+
+
+def mmc_set_tensor_projections(ctx, enable):
+    _check(lib.mmc_set_tensor_projections(ctx, int(enable)), ctx)
+
+
 def mmc_solve(ctx, b, x, nrhs, rel_tol=1e-10, precond_handle=MMC_ZERO, prec_inner=MMC_F32, m_inner=48,
               max_outer=400):
     its = ctypes.c_int()
@@ -351,6 +379,10 @@ def mmc_profile_read(ctx):
     st = mmc_profile_stats()
     _check(lib.mmc_profile_read(ctx, ctypes.byref(st)), ctx)
     return st.as_dict()
+
+
+def mmc_set_solve_params(ctx, m_inner=0, max_outer=0):
+    _check(lib.mmc_set_solve_params(ctx, int(m_inner), int(max_outer)), ctx)
 
 
 def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):

@@ -185,11 +185,12 @@ def test_double_poly(mmc, lat):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("ver,rpt", [(1, 1), (1, 2), (2, 1), (2, 2)])
+@pytest.mark.parametrize("ver,rpt,minb", [(1, 1, 1), (1, 2, 3), (2, 1, 4), (2, 1, 6), (2, 2, 3)])
 @pytest.mark.parametrize("nrhs", [5, 21])
-def test_step_kernel_variants(mmc, lat, prec, ver, rpt, nrhs):
-    """Both step-kernel versions (generic, compile-time rhs block) and lane widths give M x."""
+def test_step_kernel_variants(mmc, lat, prec, ver, rpt, minb, nrhs):
+    """Both step-kernel versions (generic, compile-time rhs block), lane widths and register caps give M x."""
     mmc.mmc_set_step_variant(lat.ctx, prec, rpt, 100 + ver, 0)
+    mmc.mmc_set_step_variant(lat.ctx, prec, 0, minb, 0)
     try:
         rng_x = synth.random_spinor(lat.dims, 9, nrhs).transpose(6, 0, 1, 2, 3, 4, 5).reshape(nrhs, -1)
         x = mmc.new_field(lat.ctx, nrhs, prec)
@@ -203,4 +204,5 @@ def test_step_kernel_variants(mmc, lat, prec, ver, rpt, nrhs):
             want = lat.op(xin[j])
             assert np.linalg.norm(got[j] - want) / np.linalg.norm(want) < tol
     finally:
-        mmc.mmc_set_step_variant(lat.ctx, prec, 2, 102, 0)
+        mmc.mmc_set_step_variant(lat.ctx, prec, 1, 102, 0)
+        mmc.mmc_set_step_variant(lat.ctx, prec, 0, 4, 0)
