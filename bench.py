@@ -203,6 +203,7 @@ def main():
             t = tune[key]
             mmc.mmc_set_step_variant(ctx, prec, t["rpt"], 100 + t["version"], t["spc"])
             mmc.mmc_set_step_variant(ctx, prec, 0, t["minb"], 0)
+            mmc.mmc_set_step_variant(ctx, prec, 0, 200 + t.get("blocked", 0), 0)
     else:
         # tuned on the batch the levels use most (512 noises); the 8-rhs solves share the choice
         tune = {"bf16_512rhs": mmc.mmc_autotune(ctx, 512, mmc.MMC_BF16),

@@ -63,6 +63,7 @@ int mmc_destroy(mmc_ctx* ctx) {
   if (ctx->links64) cudaFree(ctx->links64);
   if (ctx->links32) cudaFree(ctx->links32);
   if (ctx->nbr) cudaFree(ctx->nbr);
+  if (ctx->order) cudaFree(ctx->order);
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
   if (ctx->Z32) cudaFree(ctx->Z32);
@@ -122,6 +123,30 @@ int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiod
     }
     if (!ctx->nbr) CK(cudaMalloc(&ctx->nbr, nb.size() * sizeof(int)));
     CK(cudaMemcpy(ctx->nbr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // traversal order in 4 x 4 x 2 x 2 blocks (64 sites, one CTA chunk): neighbours mostly in-block
+    const int bl[4] = {4, 4, 2, 2};
+    bool ok = true;
+    for (int m = 0; m < 4; ++m) ok = ok && (L[m] % bl[m] == 0);
+    if (ok) {
+      std::vector<int> ord;
+      ord.reserve(V);
+      for (int bt = 0; bt < L[3] / bl[3]; ++bt)
+        for (int bz = 0; bz < L[2] / bl[2]; ++bz)
+          for (int by = 0; by < L[1] / bl[1]; ++by)
+            for (int bx = 0; bx < L[0] / bl[0]; ++bx)
+              for (int t = 0; t < bl[3]; ++t)
+                for (int z = 0; z < bl[2]; ++z)
+                  for (int y = 0; y < bl[1]; ++y)
+                    for (int x = 0; x < bl[0]; ++x) {
+                      const int X = bx * bl[0] + x, Y = by * bl[1] + y, Zc = bz * bl[2] + z, T = bt * bl[3] + t;
+                      ord.push_back(X + L[0] * (Y + L[1] * (Zc + L[2] * T)));
+                    }
+      if (!ctx->order) CK(cudaMalloc(&ctx->order, ord.size() * sizeof(int)));
+      CK(cudaMemcpy(ctx->order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice));
+    } else if (ctx->order) {
+      cudaFree(ctx->order);
+      ctx->order = nullptr;
+    }
   }
   if (!ctx->links64) CK(cudaMalloc(&ctx->links64, h64.size() * sizeof(double2)));
   if (!ctx->links32) CK(cudaMalloc(&ctx->links32, h32.size() * sizeof(float2)));
@@ -184,7 +209,10 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer) {
 
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
   if (!ctx || prec < 0 || prec > 2) return MMC_ERR_ARG;
-  if (minb >= 100) {  // minb = 100 + v selects kernel version v (1: generic, 2: compile-time rhs block)
+  if (minb >= 200) {  // minb = 200 + b: traverse sites in 4D blocks (b = 1) or lexicographically (b = 0)
+    ctx->use_order = (minb - 200) != 0;
+    minb = 0;
+  } else if (minb >= 100) {  // minb = 100 + v selects kernel version v (1: generic, 2: compile-time rhs block)
     ctx->var_ver[prec] = minb - 100;
     minb = 0;
   }
@@ -224,8 +252,11 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   double best_ms = 1e300;
   int br = ctx->var_rpt[prec], bm = ctx->var_minb[prec], bs = ctx->spc_step, bv = ctx->var_ver[prec];
   const bool v2ok = prec != MMC_F64 && (g.R == 8 || g.R == 16);
+  bool bo = ctx->use_order;
+  for (int ordr = 0; ordr <= ((v2ok && ctx->order) ? 1 : 0); ++ordr)
   for (int ver = 1; ver <= (v2ok ? 2 : 1); ++ver)
   for (int ri = 0; ri < 2; ++ri) {
+    if (ordr == 1 && ver == 1) continue;  // the blocked traversal exists in the v2 kernel only
     if (prec == MMC_F64 && rpts[ri] != 1) continue;
     if (rpts[ri] > g.R) continue;
     const int nmb = ver == 1 ? 3 : (rpts[ri] == 1 ? 2 : 1);  // v2 with two rhs per lane has one cap
@@ -235,6 +266,7 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
         ctx->var_ver[prec] = ver;
         ctx->var_rpt[prec] = rpts[ri];
         ctx->var_minb[prec] = mbv;
+        ctx->use_order = ordr == 1;
         ctx->spc_step = spcs[si];
         TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
         std::vector<float> t;
@@ -254,6 +286,7 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
           bm = mbv;
           bs = spcs[si];
           bv = ver;
+          bo = ordr == 1;
         }
       }
     }
@@ -264,11 +297,13 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   ctx->var_minb[prec] = bm;
   ctx->spc_step = bs;
   ctx->var_ver[prec] = bv;
+  ctx->use_order = bo;
   if (best) {
     best[0] = br;
     best[1] = bm;
     best[2] = bs;
     best[3] = bv;
+    best[4] = bo ? 1 : 0;
   }
   if (ms_out) *ms_out = best_ms;
   return MMC_OK;

@@ -31,6 +31,7 @@ struct step_params {
   const void* links;       // F64: double2 [site][mu][9]; F32: float2 [site][mu][10]
   const int* rb_len;       // optional: steps per rhs block; blocks with step >= len exit
   const int* nbr;          // neighbour table [site][8]: x+mu (mu = 0..3), then x-mu
+  const int* order;        // optional traversal order of the sites (4D blocks); null: lexicographic
   int step;
   int V, R, logL, npad, spc;  // sites, rhs block, log2(lanes per site), padded rhs, sites per CTA
   int Lx, Ly, Lz, Lt;

@@ -82,6 +82,8 @@ struct mmc_ctx {
   int var_minb[3] = {1, 1, 1};
   int var_ver[3] = {1, 2, 2};  // 1: generic step_kernel, 2: step2_kernel (R = 8, 16; F32, BF16)
   int* nbr = nullptr;          // device neighbour table [site][8]
+  int* order = nullptr;        // device traversal order in 4D blocks (null if the extents do not allow it)
+  bool use_order = false;      // traverse sites in 4D blocks (step kernel v2)
   // profiling (mmc_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -268,6 +270,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     p.links = run.prec == MMC_F64 ? ctx->links64 : ctx->links32;
     p.rb_len = run.rb_len;
     p.nbr = ctx->nbr;
+    p.order = ctx->use_order ? ctx->order : nullptr;
     p.step = int(k);
     p.V = ctx->V;
     p.R = g.R;

@@ -56,8 +56,9 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
   const int site_begin = blockIdx.x * p.spc;
   const int site_end = min(p.V, site_begin + p.spc);
   for (int s0 = site_begin; s0 < site_end; s0 += SPP) {
-    const int site = s0 + threadIdx.x / L;
-    if (site >= site_end) continue;
+    const int pos = s0 + threadIdx.x / L;
+    if (pos >= site_end) continue;
+    const int site = p.order ? __ldg(p.order + pos) : pos;
     const int4 nf = __ldg(reinterpret_cast<const int4*>(p.nbr) + 2 * size_t(site));
     const int4 nb = __ldg(reinterpret_cast<const int4*>(p.nbr) + 2 * size_t(site) + 1);
     cx<T> acc[12][RPT];

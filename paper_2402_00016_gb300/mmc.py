@@ -390,10 +390,11 @@ def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):
 
 
 def mmc_autotune(ctx, nrhs, prec):
-    best = (ctypes.c_int * 4)()
+    best = (ctypes.c_int * 5)()
     ms = ctypes.c_double()
     _check(lib.mmc_autotune(ctx, int(nrhs), int(prec), best, ctypes.byref(ms)), ctx)
-    return {"rpt": best[0], "minb": best[1], "spc": best[2], "version": best[3], "ms": ms.value}
+    return {"rpt": best[0], "minb": best[1], "spc": best[2], "version": best[3], "blocked": best[4],
+            "ms": ms.value}
 
 
 def mmc_update_gauge(ctx, U):

@@ -65,13 +65,14 @@ def _oracle_samples(L, hi, lo, theta_name, n, level, first=0):
     return np.array([o[0] for o in out]), np.array([o[1] for o in out])
 
 
-@pytest.mark.parametrize("ver", [1, 2])
+@pytest.mark.parametrize("ver,blocked", [(1, 0), (2, 0), (2, 1)])
 @pytest.mark.parametrize("theta_name", ["1", "g4"])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5), (2, 5e-2)])
-def test_level_poly_difference(mmc, lat, theta_name, prec, tol, ver):
+def test_level_poly_difference(mmc, lat, theta_name, prec, tol, ver, blocked):
     if prec == 0 and ver == 2:
         pytest.skip("FP64 uses the generic kernel only")
     mmc.mmc_set_step_variant(lat.ctx, prec, 0, 100 + ver, 0)
+    mmc.mmc_set_step_variant(lat.ctx, prec, 0, 200 + blocked, 0)  # 4x4x2x2 blocks divide this 4x4x2x6 lattice
     b = noise.z4_noise(lat.dims, lat.seed, 0, 0, noise.TAG_GMRES).ravel()
     t1 = krylov.gmres_poly_roots(lat.op, b, 14)
     t2 = krylov.gmres_poly_roots(lat.op, b, 5)
