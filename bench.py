@@ -348,6 +348,20 @@ def main():
                      "per_level_seconds": [r["seconds"] for r in last],
                      "per_level_matvecs": [r["matvecs"] for r in last]},
     }
+    # cost-normalised efficiency: (sum_l T_l) * (sum_l s_l^2 / N_l) is invariant under scaling
+    # every N_l by the same factor, so it gives the time to reach a target error eps as
+    # product / eps^2; the plain FP64 form shares the variances (same estimator)
+    eps_target = 0.0005 * float(np.prod(W.dims))
+    var_over_n = sum(r["var_re"] / n for r, (_, _, _, n, _) in zip(last, plan))
+    t_opt = sum(r["seconds"] for r in last)
+    line["estimate"]["time_x_var"] = t_opt * var_over_n
+    line["estimate"]["eps_target"] = eps_target
+    line["estimate"]["seconds_to_eps"] = t_opt * var_over_n / eps_target ** 2
+    if plain:
+        t_plain = sum(n * t for (_, _, _, n, _), t in zip(plan, plain["seconds_per_sample_by_level"]))
+        plain["time_x_var"] = t_plain * var_over_n
+        plain["seconds_to_eps"] = t_plain * var_over_n / eps_target ** 2
+        plain["speedup_at_equal_error"] = t_plain / t_opt
     if cpu:
         line["cpu_baseline"] = cpu
     if plain:

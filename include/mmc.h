@@ -232,6 +232,40 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
                     uint32_t first_noise, uint32_t level, int prec, int precond,
                     mmc_level_stats* out, double* samples_out);
 
+/* One level of a multilevel estimate (see mmc_estimate). */
+typedef struct {
+  int hi, lo;          /* level operands, as in mmc_trace_level */
+  int deflate;         /* as in mmc_trace_level */
+  uint32_t level;      /* level id (its noise stream) */
+  int n_first;         /* noises before the first check (>= 2) */
+  int n_check;         /* noises added between checks (>= 1) */
+  int n_max;           /* most noises the level may use (>= n_first) */
+} mmc_level_spec;
+
+enum { MMC_ALLOC_EQUAL = 0, MMC_ALLOC_COST = 1 };
+
+/* Multilevel Monte Carlo estimate with adaptive noise counts (Sec. 8: each
+ * level's standard error is checked after a first batch of noises and again
+ * after every few more; Sec. 9: cost-optimal allocation as the refinement).
+ * Every level runs mmc_trace_level on consecutive noise indices first_noise,
+ * first_noise + 1, ... of its level id, so the samples do not depend on the
+ * batching.  alloc = MMC_ALLOC_EQUAL: level l stops at the first check where
+ * its standard error is at most eps / sqrt(n_levels) (or at n_max).
+ * alloc = MMC_ALLOC_COST: after the first batches, repeatedly set the targets
+ * N_l = ceil(eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)) from the sample
+ * variances V_l and per-sample costs C_l (cost[l] if cost != NULL, else the
+ * matvecs spent per sample so far), give each level below its target the
+ * shortfall rounded up to a multiple of n_check (capped at n_max), until no
+ * level grows.  Variances are of the real part (imaginary for
+ * MMC_THETA_G4).  out[n_levels] receives each level's statistics over all its
+ * samples; total[2] (may be NULL) the sum of the level values and the
+ * combined standard error sqrt(sum_l V_l / N_l).  The exact last level
+ * (mmc_trace_exact) is not included.  Errors: those of mmc_trace_level;
+ * MMC_ERR_ARG for bad counts, eps <= 0 or non-positive costs. */
+int mmc_estimate(mmc_ctx* ctx, int n_levels, const mmc_level_spec* levels, int theta_op, int prec,
+                 int precond, double eps, int alloc, const double* cost, uint32_t first_noise,
+                 mmc_level_stats* out, double* total);
+
 /* Exact Tr(Theta p_h(M)) (Sec. 6, last level): method MMC_EXACT_UNIT sums all 12V
  * unit vectors; MMC_EXACT_PROBE uses a site colouring whose equal-colour sites are
  * farther apart (periodic L1) than the degree of p_h, 12 probe vectors per colour.

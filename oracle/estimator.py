@@ -97,3 +97,70 @@ def log_averaged_relative_variance(var_method, var_ns):
 def relative_variance(var_method, var_ns):
     """Ratio of configuration-averaged variances (Sec. 4, Eq. 3)."""
     return np.mean(var_method) / np.mean(var_ns)
+
+
+# ------------------------------------------------------------ noise counts
+# Sec. 8 checks each level's standard error after a first batch of noises and
+# then after every further few; the paper states the total target
+# eps = 0.0005 V but not how it is split between levels.  Reading taken: with
+# L Monte Carlo levels each level stops at the first check where its standard
+# error is at most eps / sqrt(L), so the levels' errors combined in quadrature
+# meet eps.  Sec. 9 names cost-optimal allocation (Giles) as future work; it is
+# the alternative rule below.
+
+def equal_split_counts(streams, eps, n_first, n_check, n_max, part="re"):
+    """Noises used per level under the check-every-few stopping rule.
+
+    ``streams[l]``: that level's samples in noise order (at least n_max[l] of
+    them, or as many as the rule can use); ``n_first``, ``n_check``, ``n_max``:
+    per-level lists.  Level l stops at the first n in n_first, n_first +
+    n_check, ... (capped at n_max) where stderr(streams[l][:n]) <= eps/sqrt(L).
+    """
+    L = len(streams)
+    target = eps / np.sqrt(L)
+    counts = []
+    for l, x in enumerate(streams):
+        n = min(n_first[l], n_max[l])
+        while True:
+            se = stats(x[:n], part)["stderr"]
+            if se <= target or n >= n_max[l]:
+                break
+            n = min(n + n_check[l], n_max[l])
+        counts.append(n)
+    return counts
+
+
+def giles_allocation(var, cost, eps):
+    """Real noise counts N_l = eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k).
+
+    They minimise the total cost sum_l C_l N_l subject to sum_l V_l / N_l =
+    eps^2 (Lagrange multiplier: C_l N_l^2 / V_l is the same for every level).
+    """
+    var = np.asarray(var, dtype=np.float64)
+    cost = np.asarray(cost, dtype=np.float64)
+    s = np.sum(np.sqrt(var * cost))
+    return np.sqrt(var / cost) * s / eps**2
+
+
+def cost_optimal_counts(streams, costs, eps, n_first, n_check, n_max, part="re"):
+    """Noises used per level when the counts follow the cost-optimal allocation.
+
+    Pilot: n_first[l] noises per level.  Then repeatedly: sample variances V_l
+    from the samples so far, targets N_l = ceil(giles_allocation(V, C, eps));
+    each level below its target gets the shortfall rounded up to a multiple of
+    n_check[l], capped at n_max[l]; stop when no level gets more.  ``costs``:
+    cost of one sample per level (fixed).
+    """
+    counts = [min(f, m) for f, m in zip(n_first, n_max)]
+    while True:
+        var = [stats(x[:n], part)["var"] for x, n in zip(streams, counts)]
+        target = np.ceil(giles_allocation(var, costs, eps))
+        grew = False
+        for l in range(len(streams)):
+            short = int(target[l]) - counts[l]
+            if short > 0 and counts[l] < n_max[l]:
+                add = -(-short // n_check[l]) * n_check[l]
+                counts[l] = min(counts[l] + add, n_max[l])
+                grew = True
+        if not grew:
+            return counts

@@ -470,6 +470,91 @@ __global__ void vec_update_kernel(geom g, const double2* Vv, int k, const double
   }
 }
 
+// FP32 forms of the two kernels above for the corrections inside refined solves
+// (the outer FP64 residual absorbs their rounding).  The vectors v_i are FP32
+// copies; each thread owns one (site, rhs), keeps its 12 field components in
+// registers, and takes the eigenvectors in chunks of kVc with one CTA reduction
+// per chunk, so the field is read once per chunk from L1 and every v_i once.
+constexpr int kVc = 8;
+
+template <typename T>
+__global__ void vec_proj32_kernel(geom g, const float2* Vv, int k, const T* f, int spc, double2* partial) {
+  __shared__ double2 sh[8 * 32];
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int spp = blockDim.x / g.R;
+  const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
+  const size_t n = size_t(g.V) * 12;
+  for (int i0 = 0; i0 < k; i0 += kVc) {
+    float2 acc[kVc];
+#pragma unroll
+    for (int q = 0; q < kVc; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int s0 = s_begin; s0 < s_end; s0 += spp) {
+      const int site = s0 + threadIdx.x / g.R;
+      if (site >= s_end) continue;
+      float2 x[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        const double2 v = get<T>(f, fidx(g, rb, site, c, r));
+        x[c] = make_float2(float(v.x), float(v.y));
+      }
+#pragma unroll
+      for (int q = 0; q < kVc; ++q) {
+        if (i0 + q >= k) break;
+        const float2* vi = Vv + size_t(i0 + q) * n + size_t(site) * 12;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          const float2 v = __ldg(vi + c);
+          acc[q].x = fmaf(v.x, x[c].x, fmaf(v.y, x[c].y, acc[q].x));
+          acc[q].y = fmaf(v.x, x[c].y, fmaf(-v.y, x[c].x, acc[q].y));
+        }
+      }
+    }
+#pragma unroll 1
+    for (int q = 0; q < kVc && i0 + q < k; ++q) {
+      double re = acc[q].x, im = acc[q].y;
+      cta_reduce_r(re, im, g.R, sh);
+      if (threadIdx.x < g.R)
+        partial[(size_t(blockIdx.x) * k + i0 + q) * g.npad + rb * g.R + threadIdx.x] = make_double2(re, im);
+    }
+  }
+}
+
+template <typename T>
+__global__ void vec_update32_kernel(geom g, const float2* Vv, int k, const double2* coef, T* f) {
+  extern __shared__ float2 sc[];  // [k][R] coefficients of this rhs block
+  const int rb = blockIdx.y;
+  for (int e = threadIdx.x; e < k * g.R; e += blockDim.x) {
+    const double2 h = coef[size_t(e / g.R) * g.npad + rb * g.R + e % g.R];
+    sc[e] = make_float2(float(h.x), float(h.y));
+  }
+  __syncthreads();
+  const int r = threadIdx.x % g.R;
+  const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
+  if (site >= g.V) return;
+  const size_t n = size_t(g.V) * 12;
+  float2 acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int i = 0; i < k; ++i) {
+    const float2 h = sc[i * g.R + r];
+    const float2* vi = Vv + size_t(i) * n + size_t(site) * 12;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const float2 v = __ldg(vi + c);
+      acc[c].x = fmaf(v.x, h.x, fmaf(-v.y, h.y, acc[c].x));
+      acc[c].y = fmaf(v.x, h.y, fmaf(v.y, h.x, acc[c].y));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    const size_t e = fidx(g, rb, site, c, r);
+    const double2 y = get<T>(f, e);
+    put<T>(f, e, y.x + double(acc[c].x), y.y + double(acc[c].y));
+  }
+}
+
 __global__ void add2_kernel(const double2* a, const double2* b, double2* out, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = make_double2(a[i].x + b[i].x, a[i].y + b[i].y);
@@ -679,6 +764,30 @@ cudaError_t launch_vec_update(int prec, geom g, const double2* Vv, int k, const 
     vec_update_kernel<double2><<<grid, 256, 0, s>>>(g, Vv, k, coef, (double2*)f);
   else
     vec_update_kernel<float2><<<grid, 256, 0, s>>>(g, Vv, k, coef, (float2*)f);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_proj32(int prec, geom g, const float2* Vv, int k, const void* f, int spc, double2* partial,
+                              cudaStream_t s) {
+  dim3 grid((g.V + spc - 1) / spc, g.nrb);
+  if (prec == 0)
+    vec_proj32_kernel<double2><<<grid, 256, 0, s>>>(g, Vv, k, (const double2*)f, spc, partial);
+  else
+    vec_proj32_kernel<float2><<<grid, 256, 0, s>>>(g, Vv, k, (const float2*)f, spc, partial);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_update32(int prec, geom g, const float2* Vv, int k, const double2* coef, void* f,
+                                cudaStream_t s) {
+  dim3 grid = site_grid(g, 256);
+  const size_t sm = size_t(k) * g.R * sizeof(float2);
+  if (sm > 48 * 1024) return cudaErrorInvalidValue;
+  if (prec == 0)
+    vec_update32_kernel<double2><<<grid, 256, sm, s>>>(g, Vv, k, coef, (double2*)f);
+  else
+    vec_update32_kernel<float2><<<grid, 256, sm, s>>>(g, Vv, k, coef, (float2*)f);
   count_launch();
   return cudaGetLastError();
 }

@@ -66,6 +66,7 @@ struct mmc_ctx {
   float2* U32 = nullptr;
   // BF16 copies [Theta z; u] for the tensor-core projections of BF16 levels, per Theta
   void* tcB[3] = {nullptr, nullptr, nullptr};
+  std::vector<mmc::cd> tc_dots[3];  // u_i^H Theta z_i from the BF16 copies (per Theta; kept with tcB)
   bool use_tc = true;
   std::map<std::string, mmc::host::DevBuf> scratch;
   // device copies of step coefficient tables, keyed by a hash of their contents:

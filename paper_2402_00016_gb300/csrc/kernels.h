@@ -79,6 +79,13 @@ cudaError_t launch_vec_proj(int prec, geom g, const double2* Vv, int k, const vo
 cudaError_t launch_vec_update(int prec, geom g, const double2* Vv, int k, const double2* coef, void* f,
                               cudaStream_t s);
 
+// FP32 forms of the two above (v_i FP32 copies, FP32 arithmetic, FP64 partials); the
+// field keeps its own precision.  k * R * 8 bytes of coefficients must fit 48 KB.
+cudaError_t launch_vec_proj32(int prec, geom g, const float2* Vv, int k, const void* f, int spc,
+                              double2* partial, cudaStream_t s);
+cudaError_t launch_vec_update32(int prec, geom g, const float2* Vv, int k, const double2* coef, void* f,
+                                cudaStream_t s);
+
 // Learned stencil network layers (net.cu).  Activations: blocked layout with 3*C
 // components per site; links: the FP32 links of the context.
 struct net_geom {

@@ -71,20 +71,29 @@ int residual_f64(mmc_ctx* ctx, const geom& g, const void* b, const void* x, void
 
 // ------------------------------------------------------------------ solves
 // x += Z Lambda^-1 U^H r for every rhs (oblique eigen-projection of the residual).
-int deflate_residual(mmc_ctx* ctx, const geom& g, const void* r, void* x, cudaStream_t s) {
+// fp32: projections and update from the FP32 copies of U and Z (inside a solve with
+// an FP32 inner stage; the next FP64 residual takes up their rounding); otherwise FP64.
+int deflate_residual(mmc_ctx* ctx, const geom& g, const void* r, void* x, bool fp32, cudaStream_t s) {
   const int k = ctx->k_defl;
   if (k == 0) return MMC_OK;
+  fp32 = fp32 && ctx->U32 && ctx->Z32 && size_t(k) * g.R * 8 <= 48 * 1024;
   const int nbx = (g.V + kSpc - 1) / kSpc;
   void* part;
   TRY(scratch(ctx, "dr_part", size_t(nbx) * k * g.npad * sizeof(double2), &part));
-  CK(mmc::launch_vec_proj(MMC_F64, g, ctx->U, k, r, kSpc, (double2*)part, s));
+  if (fp32)
+    CK(mmc::launch_vec_proj32(MMC_F64, g, (const float2*)ctx->U32, k, r, kSpc, (double2*)part, s));
+  else
+    CK(mmc::launch_vec_proj(MMC_F64, g, ctx->U, k, r, kSpc, (double2*)part, s));
   std::vector<cd> c;
   TRY(reduce_to_host(ctx, (double2*)part, nbx, k, g.npad, c, s));
   for (int i = 0; i < k; ++i)
     for (int j = 0; j < g.npad; ++j) c[size_t(i) * g.npad + j] /= ctx->lambda[i];
   void* dc;
   TRY(upload(ctx, "dr_coef", c, &dc, s));
-  CK(mmc::launch_vec_update(MMC_F64, g, ctx->Z, k, (const double2*)dc, x, s));
+  if (fp32)
+    CK(mmc::launch_vec_update32(MMC_F64, g, (const float2*)ctx->Z32, k, (const double2*)dc, x, s));
+  else
+    CK(mmc::launch_vec_update(MMC_F64, g, ctx->Z, k, (const double2*)dc, x, s));
   return MMC_OK;
 }
 
@@ -109,7 +118,7 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
   for (int outer = 0; outer <= max_outer; ++outer) {
     TRY(residual_f64(ctx, g, b, x, r, s));
     if (ctx->k_defl > 0) {
-      TRY(deflate_residual(ctx, g, r, x, s));
+      TRY(deflate_residual(ctx, g, r, x, ip != MMC_F64, s));
       TRY(residual_f64(ctx, g, b, x, r, s));
     }
     TRY(norms2(ctx, MMC_F64, g, r, rn2, s));
@@ -408,6 +417,7 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
   if (ctx->U32) cudaFree(ctx->U32);
   ctx->Z = ctx->U = nullptr;
   ctx->Z32 = ctx->U32 = nullptr;
+  for (auto& d : ctx->tc_dots) d.clear();
   for (auto& b : ctx->tcB) {
     if (b) cudaFree(b);
     b = nullptr;
@@ -477,6 +487,7 @@ int mmc_set_deflation(mmc_ctx* ctx, int k, const double* lambda, const double* Z
   if (ctx->U32) cudaFree(ctx->U32);
   ctx->Z = ctx->U = nullptr;
   ctx->Z32 = ctx->U32 = nullptr;
+  for (auto& d : ctx->tc_dots) d.clear();
   for (auto& b : ctx->tcB) {
     if (b) cudaFree(b);
     b = nullptr;
@@ -609,22 +620,62 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     TRY(scratch(ctx, "lv_b64", field_bytes(g, MMC_F64), &b64));
     TRY(scratch(ctx, "lv_x64", field_bytes(g, MMC_F64), &x64));
     CK(mmc::launch_noise(MMC_F64, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, b64, nullptr, s));
-    CK(cudaMemsetAsync(x64, 0, field_bytes(g, MMC_F64), s));
+    // With a subtracted operand the solve starts at x0 = y = A_lo eta, whose residual
+    // eta - M A_lo eta (pi_lo(M) eta for a polynomial, Sec. 3) is already small, and the
+    // sample is eta^H Theta (x - y) with x - y formed in FP64: the difference M^-1 - A_lo
+    // is never taken between two large bilinears.
+    void* y64 = nullptr;
+    if (lo != MMC_ZERO) {
+      const size_t f64 = field_bytes(g, MMC_F64);
+      TRY(scratch(ctx, "lv_y64", f64, &y64));
+      if (is_net(ctx, lo)) {
+        void *x32, *y32;
+        TRY(scratch(ctx, "lv_x32", field_bytes(g, MMC_F32), &x32));
+        TRY(scratch(ctx, "lv_y32", field_bytes(g, MMC_F32), &y32));
+        CK(mmc::launch_noise(MMC_F32, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, x32, nullptr, s));
+        TRY(net_apply(ctx, lo, x32, y32, g.npad, s, nullptr));
+        CK(mmc::launch_convert(MMC_F64, y64, MMC_F32, y32, g, s));
+      } else if (prec == MMC_F64) {
+        Run base;
+        base.g = g;
+        base.prec = prec;
+        TRY(apply_poly_impl(ctx, lo, X, n_noise, prec, ACC_Y, y64, base, s));
+      } else {
+        void* y32;
+        TRY(scratch(ctx, "lv_y32", field_bytes(g, MMC_F32), &y32));
+        Run base;
+        base.g = g;
+        base.prec = prec;
+        TRY(apply_poly_impl(ctx, lo, X, n_noise, prec, ACC_Y, y32, base, s));
+        CK(mmc::launch_convert(MMC_F64, y64, MMC_F32, y32, g, s));
+      }
+      CK(cudaMemcpyAsync(x64, y64, f64, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(cudaMemsetAsync(x64, 0, field_bytes(g, MMC_F64), s));
+    }
     std::vector<double> rel;
     int its = 0;
     // the plain FP64 form (prec = MMC_F64) solves in FP64 throughout; otherwise FP32 inner
     TRY(solve_impl(ctx, b64, x64, n_noise, 1e-10, precond, prec == MMC_F64 ? MMC_F64 : MMC_F32, ctx->solve_m,
                    ctx->solve_max_outer, &its, rel, s));
+    if (y64) {  // y <- x - y
+      std::vector<cd> one(g.npad, cd(1, 0)), minus(g.npad, cd(-1, 0));
+      void *d1, *dm;
+      TRY(upload(ctx, "lv_one", one, &d1, s));
+      TRY(upload(ctx, "lv_minus", minus, &dm, s));
+      CK(mmc::launch_axpby(MMC_F64, g, (const double2*)d1, x64, (const double2*)dm, y64, s));
+    }
     const int nb2 = (g.V + kSpc - 1) / kSpc;
     CK(cudaMemsetAsync(part, 0, size_t(nb2) * g.npad * sizeof(double2), s));
-    CK(mmc::launch_bilinear_codes(MMC_F64, g, (const uint32_t*)codes, theta_op, x64, kSpc, (double2*)part, s));
+    CK(mmc::launch_bilinear_codes(MMC_F64, g, (const uint32_t*)codes, theta_op, y64 ? y64 : x64, kSpc,
+                                  (double2*)part, s));
     std::vector<cd> v;
     TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, g.npad, v, s));
     for (int r = 0; r < g.npad; ++r) x[r] += v[r];
   } else {
     TRY(poly_bilinear(hi, 1.0));
   }
-  if (lo != MMC_ZERO) TRY(poly_bilinear(lo, -1.0));
+  if (lo != MMC_ZERO && hi != MMC_INV) TRY(poly_bilinear(lo, -1.0));
   cd corr(0, 0);
   int kd = 0;
   if (deflate && hi != MMC_INV && ctx->k_defl > 0) {
@@ -655,12 +706,14 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
       CK(cudaMemsetAsync(terr, 0, sizeof(int), s));
       CK(mmc::launch_tc_proj(g, (const uint32_t*)codes, ctx->tcB[theta_op], Kp, nsplit, (float*)tpart, (double*)tP,
                              (int*)terr, s));
-      CK(mmc::launch_tc_pair_dots(Kp, k, ctx->tcB[theta_op], (double2*)tdots, s));
+      // the exact correction's dots depend on the deflation data only: computed once per Theta
+      const bool new_dots = ctx->tc_dots[theta_op].size() != size_t(k);
+      if (new_dots) CK(mmc::launch_tc_pair_dots(Kp, k, ctx->tcB[theta_op], (double2*)tdots, s));
       std::vector<double> P(size_t(mtiles) * 128 * 256);
       std::vector<double2> dd(k);
       int herr = 0;
       CK(cudaMemcpyAsync(P.data(), tP, P.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(dd.data(), tdots, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      if (new_dots) CK(cudaMemcpyAsync(dd.data(), tdots, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (herr) RET(MMC_ERR_TIMEOUT, "mmc_trace_level: tensor-core projection wait timed out");
@@ -673,7 +726,11 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
           A[size_t(i) * g.npad + r] = cd(row0[i], -row1[i]);
           B[size_t(i) * g.npad + r] = cd(row0[128 + i], row1[128 + i]);
         }
-      for (int i = 0; i < k; ++i) D[i] = cd(dd[i].x, dd[i].y);
+      if (new_dots) {
+        ctx->tc_dots[theta_op].resize(k);
+        for (int i = 0; i < k; ++i) ctx->tc_dots[theta_op][i] = cd(dd[i].x, dd[i].y);
+      }
+      D = ctx->tc_dots[theta_op];
     } else {
       const int dp = prec == MMC_F64 ? MMC_F64 : MMC_F32;  // eigenvector copy matching the level's precision
       const void* Zd = dp == MMC_F64 ? (const void*)ctx->Z : (const void*)ctx->Z32;

@@ -26,6 +26,10 @@ def main(argv=None):
     ap.add_argument("--rpt", type=int, default=0)
     ap.add_argument("--minb", type=int, default=0)
     ap.add_argument("--spc", type=int, default=0)
+    ap.add_argument("--blocked", type=int, default=-1, help="1: 4D-blocked site traversal, 0: lexicographic")
+    ap.add_argument("--autotune", action="store_true", help="pick the kernel variant with mmc_autotune first")
+    ap.add_argument("--deflate", type=int, default=0,
+                    help="k > 0: random deflation space of k vectors, levels deflated (tensor-core projections)")
     a = ap.parse_args(argv)
     import torch
     import synth
@@ -37,16 +41,28 @@ def main(argv=None):
     try:
         mmc.mmc_load_gauge(ctx, synth.random_gauge(a.dims, 0.25, 1), 0.1565, 1)
         mmc.mmc_set_step_variant(ctx, prec, a.rpt, a.minb, a.spc)
+        if a.blocked >= 0:
+            mmc.mmc_set_step_variant(ctx, prec, 0, 200 + a.blocked, 0)
+        tuned = mmc.mmc_autotune(ctx, a.nrhs, prec) if a.autotune else None
+        if a.deflate > 0:
+            vol12 = 12 * int(np.prod(a.dims))
+            rng = np.random.default_rng(5)
+            Z = rng.standard_normal((a.deflate, vol12)) + 1j * rng.standard_normal((a.deflate, vol12))
+            Z /= np.linalg.norm(Z, axis=1, keepdims=True)
+            lam = 0.2 + 0.1j * np.arange(a.deflate)
+            mmc.mmc_set_deflation(ctx, lam, Z, Z.copy())
         # fixed Leja-ordered roots on a circle around 1 (no setup kernels before the chain)
         m = a.degree + 1
         theta = mmc.mmc_leja_order(1.0 + 0.8 * np.exp(2j * np.pi * (np.arange(m) + 0.5) / m))
         h = mmc.mmc_poly_from_roots(ctx, theta)
-        mmc.mmc_trace_level(ctx, h, mmc.MMC_ZERO, 0, 0, a.nrhs, 0, 1, prec)  # warm-up
+        h2 = mmc.mmc_poly_from_roots(ctx, theta[:2]) if a.deflate > 0 else mmc.MMC_ZERO
+        defl = 1 if a.deflate > 0 else 0
+        mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, 0, 1, prec)  # warm-up
         mmc.mmc_profile(ctx, 1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for r in range(a.reps):
-            mmc.mmc_trace_level(ctx, h, mmc.MMC_ZERO, 0, 0, a.nrhs, a.nrhs * (r + 1), 1, prec)
+            mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, a.nrhs * (r + 1), 1, prec)
         e1.record()
         torch.cuda.synchronize()
         p = mmc.mmc_profile_read(ctx)
@@ -56,7 +72,7 @@ def main(argv=None):
                "algorithmic_GBps": p["step_bytes"] / p["step_ms"] / 1e6 if p["step_ms"] else 0,
                "TFLOPs": p["step_flops"] / p["step_ms"] / 1e9 if p["step_ms"] else 0,
                "ps_per_site_rhs": 1e9 * p["step_ms"] / max(1, p["step_launches"]) / (vol * a.nrhs),
-               "wall_ms": e0.elapsed_time(e1)}
+               "wall_ms": e0.elapsed_time(e1), "variant": tuned}
         print(json.dumps(out), flush=True)
     finally:
         mmc.mmc_destroy(ctx)

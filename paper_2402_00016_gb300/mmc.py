@@ -50,6 +50,14 @@ class mmc_level_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class mmc_level_spec(ctypes.Structure):
+    _fields_ = [("hi", _i), ("lo", _i), ("deflate", _i), ("level", ctypes.c_uint32), ("n_first", _i),
+                ("n_check", _i), ("n_max", _i)]
+
+
+MMC_ALLOC_EQUAL, MMC_ALLOC_COST = 0, 1
+
+
 class mmc_profile_stats(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_longlong), ("step_ms", _d), ("step_bytes", _d), ("step_flops", _d),
                 ("all_launches", ctypes.c_longlong)]
@@ -85,6 +93,8 @@ _SIGS = {
     "mmc_trace_level": (_i, [_vp, _i, _i, _i, _i, _i, _u32, _u32, _i, _i,
                              ctypes.POINTER(mmc_level_stats), _dp]),
     "mmc_trace_exact": (_i, [_vp, _i, _i, _i, _i, _dp]),
+    "mmc_estimate": (_i, [_vp, _i, ctypes.POINTER(mmc_level_spec), _i, _i, _i, _d, _i, _dp, _u32,
+                          ctypes.POINTER(mmc_level_stats), _dp]),
     "mmc_probe_colours": (_i, [_vp, _i, _ip]),
     "mmc_net_create": (_i, [_vp, _dp, _u64, _ip]),
     "mmc_net_set_weights": (_i, [_vp, _i, _dp]),
@@ -387,6 +397,25 @@ def mmc_set_solve_params(ctx, m_inner=0, max_outer=0):
 
 def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):
     _check(lib.mmc_set_step_variant(ctx, int(prec), int(rpt), int(minb), int(spc)), ctx)
+
+
+def mmc_estimate(ctx, levels, theta_op, prec, precond, eps, alloc=MMC_ALLOC_EQUAL, cost=None, first_noise=0):
+    """levels: list of dicts with hi, lo, deflate, level, n_first, n_check, n_max.
+    Returns (per-level stats dicts, total value, total stderr)."""
+    L = len(levels)
+    specs = (mmc_level_spec * L)(*[mmc_level_spec(int(v["hi"]), int(v["lo"]), int(v.get("deflate", 0)),
+                                                  int(v["level"]), int(v["n_first"]), int(v["n_check"]),
+                                                  int(v["n_max"])) for v in levels])
+    out = (mmc_level_stats * L)()
+    tot = np.zeros(2)
+    c = None
+    if cost is not None:
+        c = np.ascontiguousarray(cost, dtype=np.float64)
+        assert c.size == L
+    _check(lib.mmc_estimate(ctx, L, specs, int(theta_op), int(prec), int(precond), float(eps), int(alloc),
+                            c.ctypes.data_as(_dp) if c is not None else None, int(first_noise), out,
+                            tot.ctypes.data_as(_dp)), ctx)
+    return [o.as_dict() for o in out], float(tot[0]), float(tot[1])
 
 
 def mmc_autotune(ctx, nrhs, prec):

@@ -198,3 +198,54 @@ def test_stats_and_relative_variance():
     assert np.isclose(s["stderr"], np.sqrt(np.var(x.real, ddof=1) / 4))
     assert np.isclose(estimator.log_averaged_relative_variance([1e-2, 1e-4], [1.0, 1.0]), 1e-3)
     assert np.isclose(estimator.relative_variance([2.0, 4.0], [6.0, 6.0]), 0.5)
+
+
+def test_equal_split_stops_at_hand_computed_count():
+    # alternating +-1 samples: even n gives stderr 1/sqrt(n-1), odd n gives sqrt(n+1)/n.
+    # Target eps / sqrt(L) = 0.25 (L = 1): checks at 3, 6, 9, 12, 15 give 0.667, 0.447,
+    # 0.351, 0.302, 0.267; n = 18 gives 0.2425, the first below 0.25.
+    x = np.array([(-1.0) ** j for j in range(100)], dtype=np.complex128)
+    assert estimator.equal_split_counts([x], 0.25, [3], [3], [100]) == [18]
+    # the cap wins, and a zero-variance level stops at its first batch
+    assert estimator.equal_split_counts([x], 0.25, [3], [3], [10]) == [10]
+    c = np.full(50, 7.0 + 1j)
+    assert estimator.equal_split_counts([c, x], 0.25 * np.sqrt(2), [6, 3], [3, 3], [50, 100]) == [6, 18]
+    # the imaginary part for gamma_4 levels
+    assert estimator.equal_split_counts([1j * x], 0.25, [3], [3], [100], part="im") == [18]
+    assert estimator.equal_split_counts([1j * x], 0.25, [3], [3], [100], part="re") == [3]
+
+
+def test_giles_allocation_minimises_cost():
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(4)
+    var = rng.uniform(0.5, 50.0, 4)
+    cost = rng.uniform(1.0, 300.0, 4)
+    eps = 0.3
+    N = estimator.giles_allocation(var, cost, eps)
+    assert np.isclose(np.sum(var / N), eps**2, rtol=1e-12)
+    # independent check: constrained minimisation of the total cost
+    res = scipy_opt.minimize(lambda n: float(np.dot(cost, n)), x0=np.full(4, 500.0),
+                             constraints=[{"type": "eq", "fun": lambda n: float(np.sum(var / n) - eps**2)}],
+                             bounds=[(1e-3, None)] * 4, method="SLSQP", options={"ftol": 1e-12, "maxiter": 500})
+    assert res.success
+    assert np.allclose(res.x, N, rtol=1e-3)
+    assert np.dot(cost, N) <= np.dot(cost, res.x) * (1 + 1e-9)
+
+
+def test_cost_optimal_counts_meet_targets():
+    # two levels of alternating samples with amplitudes 1 and 3, costs 100 and 1, eps 0.1
+    x1 = np.array([(-1.0) ** j for j in range(6000)], dtype=np.complex128)
+    x2 = 3.0 * x1
+    costs = [100.0, 1.0]
+    eps = 0.1
+    n = estimator.cost_optimal_counts([x1, x2], costs, eps, [3, 6], [3, 3], [6000, 6000])
+    # by hand: pilot variances 4/3 (3 samples) and 9 * 6/5 = 10.8 (6 samples);
+    # s = sqrt(400/3) + sqrt(10.8) = 14.83; targets ceil(sqrt(4/300) s / eps^2) = 172 and
+    # ceil(sqrt(10.8) s / eps^2) = 4875; shortfalls 169 -> 171 and 4869 (multiples of 3)
+    # give 174 and 4875; the second round (variances 174/173 and 9 * 4875/4874) asks for
+    # 131 and 3909, below both, so the counts stay
+    assert n == [174, 4875]
+    var = [estimator.stats(x1[:n[0]])["var"], estimator.stats(x2[:n[1]])["var"]]
+    target = np.ceil(estimator.giles_allocation(var, costs, eps))
+    assert all(nl >= t for nl, t in zip(n, target))
+    assert sum(v / nl for v, nl in zip(var, n)) <= eps**2
