@@ -196,14 +196,18 @@ def main():
     h["p128"], _ = mmc.mmc_gmres_poly(ctx, 129)
     h["p32"], _ = mmc.mmc_gmres_poly(ctx, 33)
     h["p8"], _ = mmc.mmc_gmres_poly(ctx, 9)
-    if args.tune_file and os.path.exists(args.tune_file):
-        with open(args.tune_file) as f:
-            tune = json.load(f)
+    if args.tune_file and (args.tune_file.lstrip().startswith("{") or os.path.exists(args.tune_file)):
+        if args.tune_file.lstrip().startswith("{"):  # the choice given inline
+            tune = json.loads(args.tune_file)
+        else:
+            with open(args.tune_file) as f:
+                tune = json.load(f)
         for key, prec in (("f32_512rhs", mmc.MMC_F32), ("bf16_512rhs", mmc.MMC_BF16)):
             t = tune[key]
             mmc.mmc_set_step_variant(ctx, prec, t["rpt"], 100 + t["version"], t["spc"])
             mmc.mmc_set_step_variant(ctx, prec, 0, t["minb"], 0)
             mmc.mmc_set_step_variant(ctx, prec, 0, 200 + t.get("blocked", 0), 0)
+            mmc.mmc_set_step_variant(ctx, prec, 0, 300 + t.get("ns", 0), 0)
     else:
         # tuned on the batch the levels use most (512 noises); the 8-rhs solves share the choice
         tune = {"bf16_512rhs": mmc.mmc_autotune(ctx, 512, mmc.MMC_BF16),

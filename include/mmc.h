@@ -338,15 +338,21 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
  * sides per lane (1, 2; F64 uses 1), minb = minimum resident CTAs per SM asked
  * of the compiler for the generic kernel (1: no register cap; 3 or 4: capped),
  * or 100 + v to select kernel version v (1: generic; 2: rhs block and epilogue
- * fixed at compile time, for F32/BF16 batches with R = 8 or 16), or 200 + b to
+ * fixed at compile time, for F32/BF16 batches with R = 8 or 16; 3: as 2, with
+ * the lattice rows staged in shared memory by bulk asynchronous copies, for
+ * Lx * R a multiple of 32 up to 512, falling back to 2 otherwise), or 200 + b to
  * traverse the sites in 4 x 4 x 2 x 2 blocks (b = 1, version 2, extents
- * divisible) or lexicographically (b = 0); spc = sites per CTA (16..1024,
- * power of two).  Values <= 0 keep the current setting. */
+ * divisible) or lexicographically (b = 0), or 300 + n to give version 3 n ring
+ * slots (2..6; 300: as many as fit); spc = sites per CTA (16..1024, power of
+ * two).  Values <= 0 keep the current setting.  Version 3 bounds every wait for
+ * its staged rows; a wait that gives up makes the next call that synchronises
+ * (a level, a solve, a reduction) return MMC_ERR_TIMEOUT. */
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc);
 /* Autotuner: time every step-kernel variant on an nrhs-vector field of
  * precision prec (random data, CUDA events, median of 3 after a warm-up),
- * keep the fastest for that precision and return it (best[5] = rpt, minb,
- * spc, kernel version, blocked traversal) with its time per launch in ms.
+ * keep the fastest for that precision and return it (best[6] = rpt, minb,
+ * spc, kernel version, blocked traversal, ring slots of version 3) with its
+ * time per launch in ms.
  * The traversal order is one setting for all precisions (the last tuning wins). */
 int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms);
 

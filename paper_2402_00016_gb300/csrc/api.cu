@@ -46,7 +46,11 @@ int mmc_create(mmc_ctx** out, const int dims[4], uint64_t seed, int device) {
   cudaError_t e = cudaSetDevice(device);
   // a blocking stream: ordered with work on the legacy default stream (where torch allocates by default)
   if (e == cudaSuccess) e = cudaStreamCreate(&ctx->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->step_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->step_err, 0, sizeof(int));
   if (e != cudaSuccess) {
+    if (ctx->step_err) cudaFree(ctx->step_err);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return MMC_ERR_CUDA;
   }
@@ -64,6 +68,7 @@ int mmc_destroy(mmc_ctx* ctx) {
   if (ctx->links32) cudaFree(ctx->links32);
   if (ctx->nbr) cudaFree(ctx->nbr);
   if (ctx->order) cudaFree(ctx->order);
+  if (ctx->step_err) cudaFree(ctx->step_err);
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
   if (ctx->Z32) cudaFree(ctx->Z32);
@@ -209,7 +214,12 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer) {
 
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
   if (!ctx || prec < 0 || prec > 2) return MMC_ERR_ARG;
-  if (minb >= 200) {  // minb = 200 + b: traverse sites in 4D blocks (b = 1) or lexicographically (b = 0)
+  if (minb >= 300) {  // minb = 300 + n: ring slots of the staged kernel (0: as many as fit)
+    const int n = minb - 300;
+    if (n != 0 && (n < 2 || n > 6)) RET(MMC_ERR_ARG, "ring slots must be 2..6 (or 0)");
+    ctx->var_ns[prec] = n;
+    minb = 0;
+  } else if (minb >= 200) {  // minb = 200 + b: traverse sites in 4D blocks (b = 1) or lexicographically (b = 0)
     ctx->use_order = (minb - 200) != 0;
     minb = 0;
   } else if (minb >= 100) {  // minb = 100 + v selects kernel version v (1: generic, 2: compile-time rhs block)
@@ -291,12 +301,42 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
       }
     }
   }
+  // the staged form (version 3) with its ring depths; rpt, caps and traversal do not apply
+  int bn = ctx->var_ns[prec];
+  if (v2ok) {
+    const int nss[3] = {0, 2, 4};
+    for (int ni = 0; ni < 3; ++ni) {
+      ctx->var_ver[prec] = 3;
+      ctx->var_ns[prec] = nss[ni];
+      ctx->use_order = false;
+      TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
+      std::vector<float> t;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(e0, s));
+        TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        t.push_back(ms);
+      }
+      TRY(check_step_err(ctx, s));
+      std::sort(t.begin(), t.end());
+      if (t[1] < best_ms) {
+        best_ms = t[1];
+        bv = 3;
+        bn = nss[ni];
+        bo = false;
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->var_rpt[prec] = br;
   ctx->var_minb[prec] = bm;
   ctx->spc_step = bs;
   ctx->var_ver[prec] = bv;
+  ctx->var_ns[prec] = bn;
   ctx->use_order = bo;
   if (best) {
     best[0] = br;
@@ -304,6 +344,7 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
     best[2] = bs;
     best[3] = bv;
     best[4] = bo ? 1 : 0;
+    best[5] = bn;
   }
   if (ms_out) *ms_out = best_ms;
   return MMC_OK;

@@ -251,20 +251,55 @@ __global__ void multidot_kernel(geom g, const T* A, size_t a_stride, int nvec, c
   }
 }
 
-__global__ void reduce_kernel(const double2* partial, int nbx, int nvec, int npad, double2* out, int accumulate) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nvec * npad) return;
-  double re = 0, im = 0;
-  for (int b = 0; b < nbx; ++b) {
-    double2 v = partial[size_t(b) * nvec * npad + idx];
-    re += v.x;
-    im += v.y;
+// out[idx] (+)= sum_b partial[b][idx] in a fixed order: a CTA of 32 x 32 threads takes 32
+// consecutive outputs; thread row j sums rows b = j, j + 32, ... with eight independent
+// accumulators (loads in flight), then the 32 row sums are added in order.
+constexpr int kRedRows = 32;
+__global__ void __launch_bounds__(1024) reduce_kernel(const double2* partial, int nbx, int nvec, int npad,
+                                                      double2* out, int accumulate) {
+  __shared__ double2 rs[kRedRows][33];
+  const int n = nvec * npad;
+  const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+  const int idx = blockIdx.x * 32 + lane;
+  double re[8], im[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) re[u] = im[u] = 0.0;
+  if (idx < n) {
+    int b = row;
+    for (; b + 7 * kRedRows < nbx; b += 8 * kRedRows) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const double2 v = partial[size_t(b + u * kRedRows) * n + idx];
+        re[u] += v.x;
+        im[u] += v.y;
+      }
+    }
+    for (; b < nbx; b += kRedRows) {
+      const double2 v = partial[size_t(b) * n + idx];
+      re[0] += v.x;
+      im[0] += v.y;
+    }
   }
-  if (accumulate) {
-    re += out[idx].x;
-    im += out[idx].y;
+  double tr = 0, ti = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    tr += re[u];
+    ti += im[u];
   }
-  out[idx] = make_double2(re, im);
+  rs[row][lane] = make_double2(tr, ti);
+  __syncthreads();
+  if (row == 0 && idx < n) {
+    double a = 0, c = 0;
+    for (int j = 0; j < kRedRows; ++j) {
+      a += rs[j][lane].x;
+      c += rs[j][lane].y;
+    }
+    if (accumulate) {
+      a += out[idx].x;
+      c += out[idx].y;
+    }
+    out[idx] = make_double2(a, c);
+  }
 }
 
 template <typename T>
@@ -668,7 +703,7 @@ cudaError_t launch_multidot(int prec, geom g, const void* A, size_t a_stride, in
 cudaError_t launch_reduce(const double2* partial, int nbx, int nvec, int npad, double2* out, int accumulate,
                           cudaStream_t s) {
   int n = nvec * npad;
-  reduce_kernel<<<(n + 127) / 128, 128, 0, s>>>(partial, nbx, nvec, npad, out, accumulate);
+  reduce_kernel<<<(n + 31) / 32, 32 * kRedRows, 0, s>>>(partial, nbx, nvec, npad, out, accumulate);
   count_launch();
   return cudaGetLastError();
 }

@@ -38,6 +38,7 @@ struct step_params {
   int tap;                 // antiperiodic time
   int theta;               // 0: 1, 1: gamma_4, 2: gamma_5
   int flags;
+  int* err;                // device flag: set by a kernel whose bounded wait gave up (staged form)
 };
 
 template <typename T>

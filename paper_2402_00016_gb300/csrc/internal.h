@@ -81,7 +81,9 @@ struct mmc_ctx {
   int spc_step = 64;  // sites per CTA of the step kernel (all precisions: partial buffers depend on it)
   int var_rpt[3] = {1, 2, 2};
   int var_minb[3] = {1, 1, 1};
-  int var_ver[3] = {1, 2, 2};  // 1: generic step_kernel, 2: step2_kernel (R = 8, 16; F32, BF16)
+  int var_ver[3] = {1, 2, 2};  // 1: generic step_kernel, 2: step2_kernel, 3: step3_kernel (R = 8, 16; F32, BF16)
+  int var_ns[3] = {0, 0, 0};   // ring slots of step3_kernel (0: as many as fit)
+  int* step_err = nullptr;     // device flag of the staged step kernel's bounded waits
   int* nbr = nullptr;          // device neighbour table [site][8]
   int* order = nullptr;        // device traversal order in 4D blocks (null if the extents do not allow it)
   bool use_order = false;      // traverse sites in 4D blocks (step kernel v2)
@@ -285,6 +287,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     p.tap = ctx->tap;
     p.theta = run.theta;
     p.flags = st.flags | (run.dagger ? mmc::SF_DAGGER : 0);
+    p.err = ctx->step_err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->prof) {
       TRY(prof_event(ctx, &e0));
@@ -292,7 +295,12 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       CK(cudaEventRecord(e0, s));
     }
     bool done = false;
-    if (ctx->var_ver[run.prec] == 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+    if (ctx->var_ver[run.prec] == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      cudaError_t e3 = cudaSuccess;
+      done = mmc::launch_step3(run.prec, g.R, run.nbx, ctx->var_ns[run.prec], p, g.nrb, s, &e3);
+      CK(e3);
+    }
+    if (!done && ctx->var_ver[run.prec] >= 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
       cudaError_t e2 = cudaSuccess;
       const int mb = ctx->var_minb[run.prec];
       done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, mb, p, g.nrb, s, &e2)
@@ -318,6 +326,19 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       ctx->prof_flops += double(ctx->V) * g.npad * (((st.flags & mmc::SF_HOP) ? 1368.0 : 0.0) + 48.0);
     }
     if (st.flags & mmc::SF_HOP) ctx->matvecs += g.npad;
+  }
+  return MMC_OK;
+}
+
+// The staged step kernel records a bounded wait that gave up in ctx->step_err; read
+// (and clear) it once the work is done.
+inline int check_step_err(mmc_ctx* ctx, cudaStream_t s) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->step_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h) {
+    CK(cudaMemsetAsync(ctx->step_err, 0, sizeof(int), s));
+    RET(MMC_ERR_TIMEOUT, "step kernel: a bounded wait for staged rows gave up");
   }
   return MMC_OK;
 }

@@ -25,7 +25,7 @@ int reduce_to_host(mmc_ctx* ctx, const double2* partial, int nbx, int nvec, int 
   CK(mmc::launch_reduce(partial, nbx, nvec, npad, (double2*)red, 0, s));
   std::vector<double2> h(size_t(nvec) * npad);
   CK(cudaMemcpyAsync(h.data(), red, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  TRY(check_step_err(ctx, s));  // synchronises
   out.resize(h.size());
   for (size_t i = 0; i < h.size(); ++i) out[i] = cd(h[i].x, h[i].y);
   return MMC_OK;

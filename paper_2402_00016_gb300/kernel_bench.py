@@ -27,6 +27,7 @@ def main(argv=None):
     ap.add_argument("--minb", type=int, default=0)
     ap.add_argument("--spc", type=int, default=0)
     ap.add_argument("--blocked", type=int, default=-1, help="1: 4D-blocked site traversal, 0: lexicographic")
+    ap.add_argument("--ns", type=int, default=-1, help="ring slots of the staged kernel (0: as many as fit)")
     ap.add_argument("--autotune", action="store_true", help="pick the kernel variant with mmc_autotune first")
     ap.add_argument("--deflate", type=int, default=0,
                     help="k > 0: random deflation space of k vectors, levels deflated (tensor-core projections)")
@@ -43,6 +44,8 @@ def main(argv=None):
         mmc.mmc_set_step_variant(ctx, prec, a.rpt, a.minb, a.spc)
         if a.blocked >= 0:
             mmc.mmc_set_step_variant(ctx, prec, 0, 200 + a.blocked, 0)
+        if a.ns >= 0:
+            mmc.mmc_set_step_variant(ctx, prec, 0, 300 + a.ns, 0)
         tuned = mmc.mmc_autotune(ctx, a.nrhs, prec) if a.autotune else None
         if a.deflate > 0:
             vol12 = 12 * int(np.prod(a.dims))

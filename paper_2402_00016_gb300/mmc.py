@@ -419,11 +419,11 @@ def mmc_estimate(ctx, levels, theta_op, prec, precond, eps, alloc=MMC_ALLOC_EQUA
 
 
 def mmc_autotune(ctx, nrhs, prec):
-    best = (ctypes.c_int * 5)()
+    best = (ctypes.c_int * 6)()
     ms = ctypes.c_double()
     _check(lib.mmc_autotune(ctx, int(nrhs), int(prec), best, ctypes.byref(ms)), ctx)
     return {"rpt": best[0], "minb": best[1], "spc": best[2], "version": best[3], "blocked": best[4],
-            "ms": ms.value}
+            "ns": best[5], "ms": ms.value}
 
 
 def mmc_update_gauge(ctx, U):

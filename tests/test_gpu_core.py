@@ -185,13 +185,28 @@ def test_double_poly(mmc, lat):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("ver,rpt,minb", [(1, 1, 1), (1, 2, 3), (2, 1, 4), (2, 1, 6), (2, 2, 3)])
+@pytest.mark.parametrize("ver,rpt,minb", [(1, 1, 1), (1, 2, 3), (2, 1, 4), (2, 1, 6), (2, 2, 3),
+                                          (3, 1, 300), (3, 1, 302)])
 @pytest.mark.parametrize("nrhs", [5, 21])
 def test_step_kernel_variants(mmc, lat, prec, ver, rpt, minb, nrhs):
-    """Both step-kernel versions (generic, compile-time rhs block), lane widths and register caps give M x."""
+    """Every step-kernel version (generic, compile-time rhs block, rows staged by bulk
+    copies with the deepest and the shallowest ring), lane widths and register caps give
+    M x, and M^+ x for the staged form."""
     mmc.mmc_set_step_variant(lat.ctx, prec, rpt, 100 + ver, 0)
     mmc.mmc_set_step_variant(lat.ctx, prec, 0, minb, 0)
     try:
+        if ver == 3:
+            rng_x = synth.random_spinor(lat.dims, 10, nrhs).transpose(6, 0, 1, 2, 3, 4, 5).reshape(nrhs, -1)
+            x = mmc.new_field(lat.ctx, nrhs, prec)
+            y = mmc.new_field(lat.ctx, nrhs, prec)
+            mmc.mmc_pack(lat.ctx, rng_x, nrhs, prec, x)
+            xin = mmc.mmc_unpack(lat.ctx, x, nrhs, prec, lat.V)
+            mmc.mmc_apply_M(lat.ctx, x, y, nrhs, prec, 1)
+            got = mmc.mmc_unpack(lat.ctx, y, nrhs, prec, lat.V)
+            tol = 1e-5 if prec == 1 else BF16_BOUND
+            for j in range(nrhs):
+                want = lat.opdag(xin[j])
+                assert np.linalg.norm(got[j] - want) / np.linalg.norm(want) < tol
         rng_x = synth.random_spinor(lat.dims, 9, nrhs).transpose(6, 0, 1, 2, 3, 4, 5).reshape(nrhs, -1)
         x = mmc.new_field(lat.ctx, nrhs, prec)
         y = mmc.new_field(lat.ctx, nrhs, prec)
@@ -206,3 +221,4 @@ def test_step_kernel_variants(mmc, lat, prec, ver, rpt, minb, nrhs):
     finally:
         mmc.mmc_set_step_variant(lat.ctx, prec, 1, 102, 0)
         mmc.mmc_set_step_variant(lat.ctx, prec, 0, 4, 0)
+        mmc.mmc_set_step_variant(lat.ctx, prec, 0, 300, 0)

@@ -65,14 +65,22 @@ def _oracle_samples(L, hi, lo, theta_name, n, level, first=0):
     return np.array([o[0] for o in out]), np.array([o[1] for o in out])
 
 
-@pytest.mark.parametrize("ver,blocked", [(1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("ver,blocked", [(1, 0), (2, 0), (2, 1), (3, 0)])
 @pytest.mark.parametrize("theta_name", ["1", "g4"])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5), (2, 5e-2)])
 def test_level_poly_difference(mmc, lat, theta_name, prec, tol, ver, blocked):
-    if prec == 0 and ver == 2:
+    if prec == 0 and ver >= 2:
         pytest.skip("FP64 uses the generic kernel only")
     mmc.mmc_set_step_variant(lat.ctx, prec, 0, 100 + ver, 0)
     mmc.mmc_set_step_variant(lat.ctx, prec, 0, 200 + blocked, 0)  # 4x4x2x2 blocks divide this 4x4x2x6 lattice
+    try:
+        _level_poly_difference(mmc, lat, theta_name, prec, tol)
+    finally:
+        mmc.mmc_set_step_variant(lat.ctx, prec, 0, 100 + (1 if prec == 0 else 2), 0)
+        mmc.mmc_set_step_variant(lat.ctx, prec, 0, 200, 0)
+
+
+def _level_poly_difference(mmc, lat, theta_name, prec, tol):
     b = noise.z4_noise(lat.dims, lat.seed, 0, 0, noise.TAG_GMRES).ravel()
     t1 = krylov.gmres_poly_roots(lat.op, b, 14)
     t2 = krylov.gmres_poly_roots(lat.op, b, 5)
@@ -194,5 +202,31 @@ def test_exact_trace_unit_and_probe(mmc):
             assert abs(got_p - ref) < 1e-11 * max(1, abs(ref))
         ncol = mmc.mmc_probe_colours(L.ctx, 2)
         assert ncol < 256
+    finally:
+        mmc.mmc_destroy(L.ctx)
+
+
+def test_extra_deflation_configuration(mmc):
+    """Sec. 8's "extra deflation": PP(70)-Arnoldi (p_in of degree 69) for 150 steps, the 60
+    smallest accepted Ritz pairs kept.  Every returned pair is an eigenpair of M to the
+    acceptance bound (residual checked with the oracle's M in FP64), the left vectors
+    are biorthonormal to the right ones, and the eigenvalues come in gamma_5 partner
+    pairs (conjugates, or real)."""
+    dims = (8, 8, 8, 8)
+    L = Lat(mmc, dims, 0.3, 0.155, seed=3)
+    try:
+        h69, _ = mmc.mmc_gmres_poly(L.ctx, 70)
+        lam = mmc.mmc_deflate(L.ctx, 60, h69, 150, 1e-3)
+        assert 10 <= len(lam) <= 60
+        lam2, Z, U = mmc.mmc_get_deflation(L.ctx, L.V)
+        assert np.allclose(lam2, lam)
+        for i in range(len(lam)):
+            z = Z[i]
+            r = L.op(z) - lam[i] * z
+            assert np.linalg.norm(r) / np.linalg.norm(z) < 1e-3
+        G = U.conj() @ Z.T
+        assert np.abs(G - np.eye(len(lam))).max() < 1e-8
+        for l in lam:
+            assert np.min(np.abs(lam - np.conj(l))) < 4e-4 + 1e-3 * abs(l)
     finally:
         mmc.mmc_destroy(L.ctx)
