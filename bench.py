@@ -8,8 +8,8 @@ eps 0.25, kappa 0.1565, antiperiodic time; levels
   Tr(p_32 - p_8)     512 noises   deflated
   Tr(p_8)            exact, by probing (setup)
 A step is one pass over all four Monte Carlo levels: 680 Z(4) samples with
-fresh noise indices, BF16 spinor storage with FP32 arithmetic, FP64
-bilinear accumulation, refined FP64 solves.  The polynomials, the deflation
+fresh noise indices, FP32 spinor storage (BF16 with --storage bf16) and FP32
+arithmetic, FP64 bilinear accumulation, refined FP64 solves.  The polynomials, the deflation
 eigenpairs and the exact last level are set up once before timing (reported
 as setup_s).  value = samples / device time (CUDA events over the timed
 steps); e2e = the same through the public API with the gauge configuration
@@ -202,16 +202,16 @@ def main():
         else:
             with open(args.tune_file) as f:
                 tune = json.load(f)
-        for key, prec in (("f32_512rhs", mmc.MMC_F32), ("bf16_512rhs", mmc.MMC_BF16)):
-            t = tune[key]
-            mmc.mmc_set_step_variant(ctx, prec, t["rpt"], 100 + t["version"], t["spc"])
-            mmc.mmc_set_step_variant(ctx, prec, 0, t["minb"], 0)
-            mmc.mmc_set_step_variant(ctx, prec, 0, 200 + t.get("blocked", 0), 0)
-            mmc.mmc_set_step_variant(ctx, prec, 0, 300 + t.get("ns", 0), 0)
+        for key, t in tune.items():
+            prec = mmc.PREC[key.split("_")[0]]
+            mmc.mmc_set_step_variant_class(ctx, prec, 1 if key.endswith("_512rhs") else 0, t)
     else:
-        # tuned on the batch the levels use most (512 noises); the 8-rhs solves share the choice
-        tune = {"bf16_512rhs": mmc.mmc_autotune(ctx, 512, mmc.MMC_BF16),
-                "f32_512rhs": mmc.mmc_autotune(ctx, 512, mmc.MMC_F32)}
+        # one variant per storage precision and rhs-block class: the 512-noise batch of the
+        # cheapest level (16-rhs blocks, every polynomial level) and the 8-rhs solves
+        tune = {}
+        for name in ("f32", "bf16"):
+            tune[name + "_512rhs"] = mmc.mmc_autotune(ctx, 512, mmc.PREC[name])
+            tune[name + "_8rhs"] = mmc.mmc_autotune(ctx, 8, mmc.PREC[name])
         if args.tune_file:
             with open(args.tune_file, "w") as f:
                 json.dump(tune, f)

@@ -184,8 +184,11 @@ int mmc_apply_poly(mmc_ctx* ctx, int handle, const void* x, void* y, int nrhs, i
  * vector (tag MMC_TAG_ARNOLDI); every Ritz vector z of phi is tested against M
  * (lambda = z^H M z, accepted if ||M z - lambda z|| < tol_accept, Sec. 8: 1e-3);
  * the accepted ones of smallest |lambda|, at most k, are kept with left vectors
- * u_i = gamma5 z_j (lambda_j = conj lambda_i; |Im| < 2e-4 counts as real) and
- * U^H Z = I.  lambda_out (2k doubles, may be NULL) receives the eigenvalues. */
+ * u_i = gamma5 z_j (lambda_j = conj lambda_i; |Im| < 2e-4 counts as real;
+ * equal eigenvalues take distinct partners) and U^H Z = I.  If the overlap
+ * W^H Z of the kept vectors is singular or its inverse exceeds 1e6, the pairs of
+ * largest |lambda| are dropped until it is not (MMC_ERR_BREAKDOWN if none is
+ * left).  lambda_out (2k doubles, may be NULL) receives the eigenvalues. */
 int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arnoldi, double tol_accept,
                 double* lambda_out, int* k_accepted);
 
@@ -334,26 +337,32 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out);
  * (defaults 48 and 400).  Values <= 0 keep the current setting. */
 int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
 
-/* Launch variant of the fused step kernel for precision prec: rpt right-hand
+/* Launch variant of the fused step kernel for precision prec, for both rhs-block
+ * classes (R < 16 and R = 16; mmc_set_step_variant_class sets one): rpt right-hand
  * sides per lane (1, 2; F64 uses 1), minb = minimum resident CTAs per SM asked
  * of the compiler for the generic kernel (1: no register cap; 3 or 4: capped),
  * or 100 + v to select kernel version v (1: generic; 2: rhs block and epilogue
  * fixed at compile time, for F32/BF16 batches with R = 8 or 16; 3: as 2, with
- * the lattice rows staged in shared memory by bulk asynchronous copies, for
- * Lx * R a multiple of 32 up to 512, falling back to 2 otherwise), or 200 + b to
- * traverse the sites in 4 x 4 x 2 x 2 blocks (b = 1, version 2, extents
- * divisible) or lexicographically (b = 0), or 300 + n to give version 3 n ring
- * slots (2..6; 300: as many as fit); spc = sites per CTA (16..1024, power of
- * two).  Values <= 0 keep the current setting.  Version 3 bounds every wait for
- * its staged rows; a wait that gives up makes the next call that synchronises
- * (a level, a solve, a reduction) return MMC_ERR_TIMEOUT. */
+ * the lattice rows staged in shared memory by bulk asynchronous copies issued
+ * by a producer warp, for Lx * R up to 384, falling back to 2 otherwise), or
+ * 200 + b to traverse the sites in 4 x 4 x 2 x 2 blocks (b = 1, version 2,
+ * extents divisible) or lexicographically (b = 0), or 300 + n to give version 3
+ * n ring slots (2..6; 300: as many as fit); spc = sites per CTA (16..1024,
+ * power of two).  Values <= 0 keep the current setting.  Version 3 bounds every
+ * wait for its staged rows; a wait that gives up makes the next call that
+ * synchronises (a level, a solve, a reduction) return MMC_ERR_TIMEOUT. */
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc);
+/* The whole variant of one rhs-block class at once: rhs_class 0 for batches
+ * whose block R is below 16 (up to 8 vectors, e.g. the solves of the M^-1
+ * level), 1 for R = 16; version 1..3 (F64: 1), rpt 1 or 2, minb 1..8, spc as
+ * above, blocked 0/1, ns 0 or 2..6.  MMC_ERR_ARG on any value out of range. */
+int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int version, int rpt, int minb, int spc,
+                               int blocked, int ns);
 /* Autotuner: time every step-kernel variant on an nrhs-vector field of
  * precision prec (random data, CUDA events, median of 3 after a warm-up),
- * keep the fastest for that precision and return it (best[6] = rpt, minb,
- * spc, kernel version, blocked traversal, ring slots of version 3) with its
- * time per launch in ms.
- * The traversal order is one setting for all precisions (the last tuning wins). */
+ * keep the fastest for that precision and the rhs-block class of nrhs and
+ * return it (best[6] = rpt, minb, spc, kernel version, blocked traversal, ring
+ * slots of version 3) with its time per launch in ms. */
 int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms);
 
 /* Replace the device links by a new host field (same layout as mmc_load_gauge)

@@ -217,24 +217,41 @@ int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
   if (minb >= 300) {  // minb = 300 + n: ring slots of the staged kernel (0: as many as fit)
     const int n = minb - 300;
     if (n != 0 && (n < 2 || n > 6)) RET(MMC_ERR_ARG, "ring slots must be 2..6 (or 0)");
-    ctx->var_ns[prec] = n;
+    ctx->var_ns[prec][0] = ctx->var_ns[prec][1] = n;
     minb = 0;
   } else if (minb >= 200) {  // minb = 200 + b: traverse sites in 4D blocks (b = 1) or lexicographically (b = 0)
-    ctx->use_order = (minb - 200) != 0;
+    ctx->order_v[prec][0] = ctx->order_v[prec][1] = (minb - 200) != 0;
     minb = 0;
   } else if (minb >= 100) {  // minb = 100 + v selects kernel version v (1: generic, 2: compile-time rhs block)
-    ctx->var_ver[prec] = minb - 100;
+    ctx->var_ver[prec][0] = ctx->var_ver[prec][1] = minb - 100;
     minb = 0;
   }
   if (rpt > 0) {
     if (rpt != 1 && rpt != 2) RET(MMC_ERR_ARG, "rpt must be 1 or 2");
-    ctx->var_rpt[prec] = prec == MMC_F64 ? 1 : rpt;
+    ctx->var_rpt[prec][0] = ctx->var_rpt[prec][1] = prec == MMC_F64 ? 1 : rpt;
   }
-  if (minb > 0) ctx->var_minb[prec] = minb;
+  if (minb > 0) ctx->var_minb[prec][0] = ctx->var_minb[prec][1] = minb;
   if (spc > 0) {
     if (spc < 16 || spc > 1024 || (spc & (spc - 1))) RET(MMC_ERR_ARG, "spc must be a power of two in 16..1024");
-    ctx->spc_step = spc;
+    ctx->spc_v[prec][0] = ctx->spc_v[prec][1] = spc;
   }
+  return MMC_OK;
+}
+
+int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int version, int rpt, int minb, int spc,
+                               int blocked, int ns) {
+  if (!ctx || prec < 0 || prec > 2 || rhs_class < 0 || rhs_class > 1) return MMC_ERR_ARG;
+  if (version < 1 || version > 3 || (prec == MMC_F64 && version != 1)) RET(MMC_ERR_ARG, "bad kernel version");
+  if (rpt != 1 && rpt != 2) RET(MMC_ERR_ARG, "rpt must be 1 or 2");
+  if (minb < 1 || minb > 8) RET(MMC_ERR_ARG, "minb must be 1..8");
+  if (spc < 16 || spc > 1024 || (spc & (spc - 1))) RET(MMC_ERR_ARG, "spc must be a power of two in 16..1024");
+  if (ns != 0 && (ns < 2 || ns > 6)) RET(MMC_ERR_ARG, "ring slots must be 2..6 (or 0)");
+  ctx->var_ver[prec][rhs_class] = version;
+  ctx->var_rpt[prec][rhs_class] = prec == MMC_F64 ? 1 : rpt;
+  ctx->var_minb[prec][rhs_class] = minb;
+  ctx->spc_v[prec][rhs_class] = spc;
+  ctx->order_v[prec][rhs_class] = blocked != 0;
+  ctx->var_ns[prec][rhs_class] = ns;
   return MMC_OK;
 }
 
@@ -260,9 +277,10 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   const int minbs2[2] = {4, 6};  // v2, one rhs per lane: 128 or 80 registers
   const int spcs[4] = {32, 64, 128, 256};
   double best_ms = 1e300;
-  int br = ctx->var_rpt[prec], bm = ctx->var_minb[prec], bs = ctx->spc_step, bv = ctx->var_ver[prec];
+  const int rc = rclass(g.R);  // the variant is kept for this rhs-block class only
+  int br = ctx->var_rpt[prec][rc], bm = ctx->var_minb[prec][rc], bs = ctx->spc_v[prec][rc], bv = ctx->var_ver[prec][rc];
   const bool v2ok = prec != MMC_F64 && (g.R == 8 || g.R == 16);
-  bool bo = ctx->use_order;
+  bool bo = ctx->order_v[prec][rc];
   for (int ordr = 0; ordr <= ((v2ok && ctx->order) ? 1 : 0); ++ordr)
   for (int ver = 1; ver <= (v2ok ? 2 : 1); ++ver)
   for (int ri = 0; ri < 2; ++ri) {
@@ -273,11 +291,11 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
     for (int mi = 0; mi < nmb; ++mi) {
       const int mbv = ver == 1 ? minbs[mi] : (rpts[ri] == 1 ? minbs2[mi] : 3);
       for (int si = 0; si < 4; ++si) {
-        ctx->var_ver[prec] = ver;
-        ctx->var_rpt[prec] = rpts[ri];
-        ctx->var_minb[prec] = mbv;
-        ctx->use_order = ordr == 1;
-        ctx->spc_step = spcs[si];
+        ctx->var_ver[prec][rc] = ver;
+        ctx->var_rpt[prec][rc] = rpts[ri];
+        ctx->var_minb[prec][rc] = mbv;
+        ctx->order_v[prec][rc] = ordr == 1;
+        ctx->spc_v[prec][rc] = spcs[si];
         TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
         std::vector<float> t;
         for (int rep = 0; rep < 3; ++rep) {
@@ -302,13 +320,16 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
     }
   }
   // the staged form (version 3) with its ring depths; rpt, caps and traversal do not apply
-  int bn = ctx->var_ns[prec];
+  int bn = ctx->var_ns[prec][rc];
   if (v2ok) {
     const int nss[3] = {0, 2, 4};
+    for (int ri = 0; ri < 2; ++ri)
     for (int ni = 0; ni < 3; ++ni) {
-      ctx->var_ver[prec] = 3;
-      ctx->var_ns[prec] = nss[ni];
-      ctx->use_order = false;
+      if (rpts[ri] > g.R) continue;
+      ctx->var_ver[prec][rc] = 3;
+      ctx->var_ns[prec][rc] = nss[ni];
+      ctx->var_rpt[prec][rc] = rpts[ri];
+      ctx->order_v[prec][rc] = false;
       TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
       std::vector<float> t;
       for (int rep = 0; rep < 3; ++rep) {
@@ -326,18 +347,19 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
         best_ms = t[1];
         bv = 3;
         bn = nss[ni];
+        br = rpts[ri];
         bo = false;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ctx->var_rpt[prec] = br;
-  ctx->var_minb[prec] = bm;
-  ctx->spc_step = bs;
-  ctx->var_ver[prec] = bv;
-  ctx->var_ns[prec] = bn;
-  ctx->use_order = bo;
+  ctx->var_rpt[prec][rc] = br;
+  ctx->var_minb[prec][rc] = bm;
+  ctx->spc_v[prec][rc] = bs;
+  ctx->var_ver[prec][rc] = bv;
+  ctx->var_ns[prec][rc] = bn;
+  ctx->order_v[prec][rc] = bo;
   if (best) {
     best[0] = br;
     best[1] = bm;

@@ -78,15 +78,16 @@ struct mmc_ctx {
   int solve_max_outer = 400;
   std::string err;
   long long matvecs = 0;
-  int spc_step = 64;  // sites per CTA of the step kernel (all precisions: partial buffers depend on it)
-  int var_rpt[3] = {1, 2, 2};
-  int var_minb[3] = {1, 1, 1};
-  int var_ver[3] = {1, 2, 2};  // 1: generic step_kernel, 2: step2_kernel, 3: step3_kernel (R = 8, 16; F32, BF16)
-  int var_ns[3] = {0, 0, 0};   // ring slots of step3_kernel (0: as many as fit)
+  int spc_v[3][2] = {{64, 64}, {64, 64}, {64, 64}};  // sites per CTA of the step kernel (per variant class)
+  // step-kernel variant per precision and rhs-block class (R < 16, R = 16)
+  int var_rpt[3][2] = {{1, 1}, {2, 2}, {2, 2}};
+  int var_minb[3][2] = {{1, 1}, {1, 1}, {1, 1}};
+  int var_ver[3][2] = {{1, 1}, {2, 2}, {2, 2}};  // 1: step_kernel, 2: step2_kernel, 3: step3_kernel (F32, BF16)
+  int var_ns[3][2] = {{0, 0}, {0, 0}, {0, 0}};   // ring slots of step3_kernel (0: as many as fit)
   int* step_err = nullptr;     // device flag of the staged step kernel's bounded waits
   int* nbr = nullptr;          // device neighbour table [site][8]
   int* order = nullptr;        // device traversal order in 4D blocks (null if the extents do not allow it)
-  bool use_order = false;      // traverse sites in 4D blocks (step kernel v2)
+  bool order_v[3][2] = {{false, false}, {false, false}, {false, false}};  // 4D-blocked traversal (v2)
   // profiling (mmc_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -161,9 +162,11 @@ inline int scratch(mmc_ctx* ctx, const std::string& key, size_t bytes, void** ou
   return MMC_OK;
 }
 
+inline int rclass(int R) { return R >= 16 ? 1 : 0; }
+
 inline int rpt_for(const mmc_ctx* ctx, int prec, int R) {
   if (prec == MMC_F64) return 1;
-  return std::min(ctx->var_rpt[prec], R);
+  return std::min(ctx->var_rpt[prec][rclass(R)], R);
 }
 
 inline int log2i(int v) {
@@ -196,6 +199,15 @@ struct Run {
 };
 
 inline int nbx_for(const mmc_ctx* ctx, int spc) { return (ctx->V + spc - 1) / spc; }
+// Rows of the bilinear partial buffers of a step chain: one per CTA of the site-chunked
+// forms (the smallest sites-per-CTA of any variant), one per compute warp of the staged
+// form (up to 16 warps on each of 152 SMs).
+inline int nbx_step(const mmc_ctx* ctx) {
+  int spc = 1 << 30;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 2; ++b) spc = std::min(spc, ctx->spc_v[a][b]);
+  return std::max(nbx_for(ctx, spc), 152 * 16);
+}
 
 inline int prof_event(mmc_ctx* ctx, cudaEvent_t* e) {
   if (ctx->ev_pool.empty()) {
@@ -273,13 +285,13 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     p.links = run.prec == MMC_F64 ? ctx->links64 : ctx->links32;
     p.rb_len = run.rb_len;
     p.nbr = ctx->nbr;
-    p.order = ctx->use_order ? ctx->order : nullptr;
+    p.order = ctx->order_v[run.prec][rclass(g.R)] ? ctx->order : nullptr;
     p.step = int(k);
     p.V = ctx->V;
     p.R = g.R;
     p.logL = log2i(g.R / rpt);
     p.npad = g.npad;
-    p.spc = ctx->spc_step;
+    p.spc = ctx->spc_v[run.prec][rclass(g.R)];
     p.Lx = ctx->dims[0];
     p.Ly = ctx->dims[1];
     p.Lz = ctx->dims[2];
@@ -295,19 +307,20 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       CK(cudaEventRecord(e0, s));
     }
     bool done = false;
-    if (ctx->var_ver[run.prec] == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+    const int rc = rclass(g.R);
+    if (ctx->var_ver[run.prec][rc] == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
       cudaError_t e3 = cudaSuccess;
-      done = mmc::launch_step3(run.prec, g.R, run.nbx, ctx->var_ns[run.prec], p, g.nrb, s, &e3);
+      done = mmc::launch_step3(run.prec, g.R, rpt, run.nbx, ctx->var_ns[run.prec][rc], p, g.nrb, s, &e3);
       CK(e3);
     }
-    if (!done && ctx->var_ver[run.prec] >= 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+    if (!done && ctx->var_ver[run.prec][rc] >= 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
       cudaError_t e2 = cudaSuccess;
-      const int mb = ctx->var_minb[run.prec];
+      const int mb = ctx->var_minb[run.prec][rc];
       done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, mb, p, g.nrb, s, &e2)
                                  : mmc::launch_step2_bf16(g.R, rpt, mb, p, g.nrb, s, &e2);
       CK(e2);
     }
-    if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec], p, g.nrb, s));
+    if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec][rc], p, g.nrb, s));
     if (ctx->prof) {
       CK(cudaEventRecord(e1, s));
       ctx->ev_pending.push_back({e0, e1});

@@ -26,9 +26,10 @@ cudaError_t launch_step(int prec, int rpt, int minb, const step_params& p, int n
 bool launch_step2_f32(int R, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
 bool launch_step2_bf16(int R, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
 // Staged form (rows by bulk asynchronous copies, stencil3.cuh) for FP32 (prec 1) and BF16
-// (prec 2) storage, R = 8 or 16; nbx: rows of the bilinear partials (grid bound), ns: ring
-// slots (0: as many as fit).  Returns false when the geometry or flags need another form.
-bool launch_step3(int prec, int R, int nbx, int ns, const step_params& p, int n_rb, cudaStream_t s,
+// (prec 2) storage, R = 8 or 16, rpt = 1 or 2 rhs per thread; nbx: rows of the bilinear
+// partials (grid bound), ns: ring slots (0: as many as fit).  Returns false when the
+// geometry or flags need another form.
+bool launch_step3(int prec, int R, int rpt, int nbx, int ns, const step_params& p, int n_rb, cudaStream_t s,
                   cudaError_t* err);
 
 // Z(4) noise (Sec. 1) into a field of precision prec and/or packed codes.

@@ -387,7 +387,11 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
   if (int(acc.size()) > k) acc.resize(k);
   // left vectors from gamma5-hermiticity: partner with conj(lambda), |Im| < 2e-4 counts as real
   const double real_tol = 2e-4;
+  // A degenerate eigenvalue gives several accepted vectors with (nearly) equal lambda:
+  // each takes a different partner (the nearest one not yet taken), so the left
+  // vectors stay independent.
   std::vector<int> keep, partner;
+  std::vector<char> taken(m_arn, 0);
   for (size_t a = 0; a < acc.size(); ++a) {
     cd l = lam[acc[a]];
     if (std::abs(l.imag()) < real_tol) {
@@ -398,7 +402,7 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
     int best = -1;
     double bd = 1e300;
     for (size_t b2 = 0; b2 < acc.size(); ++b2) {
-      if (b2 == a) continue;
+      if (b2 == a || taken[acc[b2]]) continue;
       double d = std::abs(lam[acc[b2]] - std::conj(l));
       if (d < bd) {
         bd = d;
@@ -408,9 +412,10 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
     if (best >= 0 && bd < std::max(real_tol, 1e-6 * std::abs(l)) * 10) {
       keep.push_back(acc[a]);
       partner.push_back(best);
+      taken[best] = 1;
     }
   }
-  const int kk = int(keep.size());
+  int kk = int(keep.size());
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
   if (ctx->Z32) cudaFree(ctx->Z32);
@@ -444,11 +449,20 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
       TRY(reduce_to_host(ctx, (double2*)part, nbx, kk, 1, col, s));
       for (int i = 0; i < kk; ++i) S(i, j) = col[i];
     }
-    CMat SH(kk, kk), Inv(kk, kk);
-    for (int i = 0; i < kk; ++i)
-      for (int j = 0; j < kk; ++j) SH(i, j) = std::conj(S(j, i));
-    for (int i = 0; i < kk; ++i) Inv(i, i) = 1.0;
-    if (!mmc::lu_solve(SH, Inv)) RET(MMC_ERR_BREAKDOWN, "mmc_deflate: W^H Z is singular");
+    // a singular or ill-conditioned overlap drops the pairs of largest |lambda| until it is not
+    CMat Inv;
+    for (; kk > 0; --kk) {
+      CMat SH(kk, kk);
+      Inv = CMat(kk, kk);
+      for (int i = 0; i < kk; ++i)
+        for (int j = 0; j < kk; ++j) SH(i, j) = std::conj(S(j, i));
+      for (int i = 0; i < kk; ++i) Inv(i, i) = 1.0;
+      if (!mmc::lu_solve(SH, Inv)) continue;
+      double big = 0;  // |u_i| grows with 1/|S|
+      for (const cd& v : Inv.a) big = std::max(big, std::abs(v));
+      if (big < 1e6) break;
+    }
+    if (kk == 0) RET(MMC_ERR_BREAKDOWN, "mmc_deflate: W^H Z is singular");
     // Inv = S^{-H};  U_i = sum_j W_j Inv(j, i)
     for (int i = 0; i < kk; ++i) {
       std::vector<cd> h(kk);
@@ -574,7 +588,7 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
   const long long mv0 = ctx->matvecs;
   cudaStream_t s = ctx->stream;
   const geom g = make_geom(ctx, n_noise);
-  const int nbx = nbx_for(ctx, ctx->spc_step);
+  const int nbx = nbx_step(ctx);
   void *codes, *X, *part, *dids;
   TRY(scratch(ctx, "lv_codes", size_t(g.npad) * g.V * sizeof(uint32_t), &codes));
   TRY(scratch(ctx, "lv_X", field_bytes(g, prec), &X));
@@ -819,7 +833,7 @@ int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec
   const long long nprobe = (long long)col.n * 12;
   const int batch = int(std::min<long long>(nprobe, 256));
   const geom g = make_geom(ctx, batch);
-  const int nbx = nbx_for(ctx, ctx->spc_step);
+  const int nbx = nbx_step(ctx);
   void *dcol, *dpr, *X, *part;
   TRY(scratch(ctx, "ex_col", size_t(ctx->V) * sizeof(int), &dcol));
   CK(cudaMemcpyAsync(dcol, col.colour.data(), size_t(ctx->V) * sizeof(int), cudaMemcpyHostToDevice, s));

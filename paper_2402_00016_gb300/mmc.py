@@ -106,6 +106,7 @@ _SIGS = {
     "mmc_profile_read": (_i, [_vp, ctypes.POINTER(mmc_profile_stats)]),
     "mmc_update_gauge": (_i, [_vp, _dp]),
     "mmc_set_step_variant": (_i, [_vp, _i, _i, _i, _i]),
+    "mmc_set_step_variant_class": (_i, [_vp, _i, _i, _i, _i, _i, _i, _i, _i]),
     "mmc_set_solve_params": (_i, [_vp, _i, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
     "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
@@ -397,6 +398,13 @@ def mmc_set_solve_params(ctx, m_inner=0, max_outer=0):
 
 def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):
     _check(lib.mmc_set_step_variant(ctx, int(prec), int(rpt), int(minb), int(spc)), ctx)
+
+
+def mmc_set_step_variant_class(ctx, prec, rhs_class, v):
+    """v: a dict as returned by mmc_autotune (rpt, minb, spc, version, blocked, ns)."""
+    _check(lib.mmc_set_step_variant_class(ctx, int(prec), int(rhs_class), int(v["version"]), int(v["rpt"]),
+                                          int(v["minb"]), int(v["spc"]), int(v.get("blocked", 0)),
+                                          int(v.get("ns", 0))), ctx)
 
 
 def mmc_estimate(ctx, levels, theta_op, prec, precond, eps, alloc=MMC_ALLOC_EQUAL, cost=None, first_noise=0):

@@ -186,11 +186,12 @@ def test_double_poly(mmc, lat):
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("ver,rpt,minb", [(1, 1, 1), (1, 2, 3), (2, 1, 4), (2, 1, 6), (2, 2, 3),
-                                          (3, 1, 300), (3, 1, 302)])
+                                          (3, 1, 300), (3, 1, 302), (3, 2, 300)])
 @pytest.mark.parametrize("nrhs", [5, 21])
 def test_step_kernel_variants(mmc, lat, prec, ver, rpt, minb, nrhs):
     """Every step-kernel version (generic, compile-time rhs block, rows staged by bulk
-    copies with the deepest and the shallowest ring), lane widths and register caps give
+    copies with the deepest and the shallowest ring, one or two rhs per lane), lane widths
+    and register caps give
     M x, and M^+ x for the staged form."""
     mmc.mmc_set_step_variant(lat.ctx, prec, rpt, 100 + ver, 0)
     mmc.mmc_set_step_variant(lat.ctx, prec, 0, minb, 0)
@@ -218,6 +219,36 @@ def test_step_kernel_variants(mmc, lat, prec, ver, rpt, minb, nrhs):
         for j in range(nrhs):
             want = lat.op(xin[j])
             assert np.linalg.norm(got[j] - want) / np.linalg.norm(want) < tol
+    finally:
+        mmc.mmc_set_step_variant(lat.ctx, prec, 1, 102, 0)
+        mmc.mmc_set_step_variant(lat.ctx, prec, 0, 4, 0)
+        mmc.mmc_set_step_variant(lat.ctx, prec, 0, 300, 0)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_step_variant_per_rhs_class(mmc, lat, prec):
+    """The 8-rhs class and the 16-rhs class keep separate variants: a batch of each runs
+    with its own kernel form and both give M x; out-of-range settings are rejected."""
+    staged = {"version": 3, "rpt": 2, "minb": 1, "spc": 64, "blocked": 0, "ns": 0}
+    plain = {"version": 2, "rpt": 1, "minb": 4, "spc": 32, "blocked": 0, "ns": 0}
+    try:
+        mmc.mmc_set_step_variant_class(lat.ctx, prec, 0, staged)
+        mmc.mmc_set_step_variant_class(lat.ctx, prec, 1, plain)
+        for nrhs in (6, 19):
+            rng_x = synth.random_spinor(lat.dims, 12, nrhs).transpose(6, 0, 1, 2, 3, 4, 5).reshape(nrhs, -1)
+            x = mmc.new_field(lat.ctx, nrhs, prec)
+            y = mmc.new_field(lat.ctx, nrhs, prec)
+            mmc.mmc_pack(lat.ctx, rng_x, nrhs, prec, x)
+            xin = mmc.mmc_unpack(lat.ctx, x, nrhs, prec, lat.V)
+            mmc.mmc_apply_M(lat.ctx, x, y, nrhs, prec, 0)
+            got = mmc.mmc_unpack(lat.ctx, y, nrhs, prec, lat.V)
+            tol = 1e-5 if prec == 1 else BF16_BOUND
+            for j in range(nrhs):
+                want = lat.op(xin[j])
+                assert np.linalg.norm(got[j] - want) / np.linalg.norm(want) < tol
+        for bad in ({"rpt": 3}, {"version": 4}, {"ns": 7}, {"spc": 48}):
+            with pytest.raises(mmc.MMCError):
+                mmc.mmc_set_step_variant_class(lat.ctx, prec, 0, dict(staged, **bad))
     finally:
         mmc.mmc_set_step_variant(lat.ctx, prec, 1, 102, 0)
         mmc.mmc_set_step_variant(lat.ctx, prec, 0, 4, 0)
