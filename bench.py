@@ -157,6 +157,9 @@ def main():
     ap.add_argument("--deflate-k", type=int, default=100)
     ap.add_argument("--arnoldi", type=int, default=200)
     ap.add_argument("--solve-m", type=int, default=16, help="inner FGMRES length of the M^-1 level solves")
+    ap.add_argument("--precond", default="in", choices=["in", "dbl"],
+                    help="right preconditioner of those solves: the inner GMRES polynomial (degree 39) or the "
+                         "double polynomial (degree 319)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
                     help="spinor storage of the polynomial chains (BF16 rounding shifts the level samples by "
                          "several standard errors on this workload: see error_vs_fp64)")
@@ -218,6 +221,7 @@ def main():
     mmc.mmc_set_solve_params(ctx, args.solve_m, 400)
     t_poly = time.time() - t_setup
     lam = mmc.mmc_deflate(ctx, args.deflate_k, h["in"], args.arnoldi, 1e-3) if args.deflate_k > 0 else []
+    pre = h[args.precond]
     t_defl = time.time() - t_setup - t_poly
     exact = mmc.mmc_trace_exact(ctx, h["p8"], mmc.MMC_THETA_ONE, mmc.MMC_EXACT_PROBE, mmc.MMC_F64)
     ncol = mmc.mmc_probe_colours(ctx, 8)
@@ -229,7 +233,7 @@ def main():
         for (hi, lo, defl, n, lvl) in plan:
             first = replicas.noise_first(it, rank, world, n)
             out.append(mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, n, first, lvl, storage,
-                                           h["in"], want_samples=True))
+                                           pre, want_samples=True))
         return out
 
     def barrier():
@@ -287,7 +291,7 @@ def main():
         for (hi, lo, defl, n, lvl) in plan:
             torch.cuda.synchronize()
             t0 = time.time()
-            mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, 1, 900_000, lvl, mmc.MMC_F64, h["in"],
+            mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, 1, 900_000, lvl, mmc.MMC_F64, pre,
                                 want_samples=False)
             torch.cuda.synchronize()
             per_sample.append(time.time() - t0)
@@ -304,8 +308,8 @@ def main():
         err_vs_fp64 = []
         for (hi, lo, defl, n, lvl), r in zip(plan, last):
             q = 1 if hi == mmc.MMC_INV else min(n, 4)  # the FP64 solves are the costly part
-            a = mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, q, 800_000, lvl, storage, h["in"])
-            b = mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, q, 800_000, lvl, mmc.MMC_F64, h["in"])
+            a = mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, q, 800_000, lvl, storage, pre)
+            b = mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, q, 800_000, lvl, mmc.MMC_F64, pre)
             d = a["samples"] - b["samples"]
             se = float(np.sqrt(r["var_re"] / n)) if r["var_re"] > 0 else float("nan")
             err_vs_fp64.append({"noises": q, "max_abs_sample_diff": float(np.abs(d).max()),
@@ -331,7 +335,9 @@ def main():
         "config": {"workload": WORKLOAD, "lattice": "24^4", "eps": W.eps, "kappa": W.kappa,
                    "levels": ["M^-1 - p_dbl(40x8)", "p_dbl - p_128", "p_128 - p_32", "p_32 - p_8"],
                    "noises": [8, 32, 128, 512], "storage": args.storage, "arithmetic": "fp32, fp64 bilinears",
-                   "deflated": len(lam), "probe_colours": ncol, "l2": "inputs larger than L2 (GB-sized fields)",
+                   "deflated": len(lam), "probe_colours": ncol,
+                   "solves": {"fgmres_m": args.solve_m, "precond": "p_in (degree 39)" if args.precond == "in"
+                              else "p_dbl (degree 319)", "tol": 1e-10}, "l2": "inputs larger than L2 (GB-sized fields)",
                    "parallelism": "replicas" if world > 1 else "1 gpu"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "step_kernel (fused stencil + Leja step)",
