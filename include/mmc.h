@@ -358,6 +358,20 @@ int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc);
  * above, blocked 0/1, ns 0 or 2..6.  MMC_ERR_ARG on any value out of range. */
 int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int version, int rpt, int minb, int spc,
                                int blocked, int ns);
+/* Step chains (the degrees of a polynomial applied to a batch, Sec. 3, Sec. 5) run
+ * as CUDA graphs: the first run of a chain with given operands, coefficients and
+ * kernel variant captures its launches, later runs replay the graph (one launch
+ * for all degrees).  enable = 0 launches every degree directly (and drops the
+ * graphs); results are identical either way.  Default: enabled.  A chain called
+ * while the caller's stream is already capturing is launched directly into the
+ * caller's capture. */
+int mmc_set_graphs(mmc_ctx* ctx, int enable);
+/* enable != 0 (the default): the step kernels read and write the operands that a
+ * launch touches once (the result, the auxiliary operand, the accumulator, the
+ * left field, the noise codes) with evict-first cache hints, so that L2 keeps the
+ * iterate, each element of which is read by nine sites.  Results are identical
+ * either way. */
+int mmc_set_stream_hints(mmc_ctx* ctx, int enable);
 /* Autotuner: time every step-kernel variant on an nrhs-vector field of
  * precision prec (random data, CUDA events, median of 3 after a warm-up),
  * keep the fastest for that precision and the rhs-block class of nrhs and

@@ -76,6 +76,7 @@ int mmc_destroy(mmc_ctx* ctx) {
   for (auto b : ctx->tcB)
     if (b) cudaFree(b);
   prof_collect(ctx);
+  clear_graphs(ctx);
   for (auto& kv : ctx->coef_cache) cudaFree(kv.second.p);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -235,6 +236,23 @@ int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
     if (spc < 16 || spc > 1024 || (spc & (spc - 1))) RET(MMC_ERR_ARG, "spc must be a power of two in 16..1024");
     ctx->spc_v[prec][0] = ctx->spc_v[prec][1] = spc;
   }
+  return MMC_OK;
+}
+
+int mmc_set_graphs(mmc_ctx* ctx, int enable) {
+  if (!ctx) return MMC_ERR_ARG;
+  if (!enable && ctx->use_graphs) {
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    clear_graphs(ctx);
+  }
+  ctx->use_graphs = enable != 0;
+  return MMC_OK;
+}
+
+int mmc_set_stream_hints(mmc_ctx* ctx, int enable) {
+  if (!ctx) return MMC_ERR_ARG;
+  ctx->stream_hints = enable != 0;
   return MMC_OK;
 }
 

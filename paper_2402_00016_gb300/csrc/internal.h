@@ -74,6 +74,16 @@ struct mmc_ctx {
   // table without a host-to-device copy or a stream synchronisation
   std::map<uint64_t, mmc::host::DevBuf> coef_cache;
   size_t coef_cache_bytes = 0;
+  // CUDA graphs of step chains, keyed by a hash of everything that decides their
+  // launches (coefficient table, operand pointers, flags, kernel variant): a chain
+  // run again with the same buffers replays its graph (one launch for all degrees)
+  struct ChainGraph {
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;  // kernel launches captured (for the launch counter)
+  };
+  std::map<uint64_t, ChainGraph> graph_cache;
+  bool use_graphs = true;
+  bool stream_hints = true;  // evict-first hints on once-touched step operands (SF_STREAM)
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
   std::string err;
@@ -234,6 +244,12 @@ inline int prof_collect(mmc_ctx* ctx) {
   return MMC_OK;
 }
 
+inline void clear_graphs(mmc_ctx* ctx) {
+  for (auto& kv : ctx->graph_cache)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  ctx->graph_cache.clear();
+}
+
 inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
   if (run.steps.empty()) return MMC_OK;
   const geom& g = run.g;
@@ -260,6 +276,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       for (auto& kv : ctx->coef_cache) cudaFree(kv.second.p);
       ctx->coef_cache.clear();
       ctx->coef_cache_bytes = 0;
+      clear_graphs(ctx);
     }
     DevBuf b;
     CK(cudaMalloc(&b.p, nb));
@@ -270,61 +287,139 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     dcoef = b.p;
   }
   const int rpt = rpt_for(ctx, run.prec, g.R);
-  for (size_t k = 0; k < run.steps.size(); ++k) {
-    const Step& st = run.steps[k];
-    mmc::step_params p;
-    std::memset(&p, 0, sizeof(p));
-    p.in = st.in;
-    p.out = st.out;
-    p.aux = st.aux;
-    p.y = run.y;
-    p.codes = run.codes;
-    p.left = run.left;
-    p.coef = reinterpret_cast<const double2*>(dcoef) + k * per;
-    p.partial = run.partial;
-    p.links = run.prec == MMC_F64 ? ctx->links64 : ctx->links32;
-    p.rb_len = run.rb_len;
-    p.nbr = ctx->nbr;
-    p.order = ctx->order_v[run.prec][rclass(g.R)] ? ctx->order : nullptr;
-    p.step = int(k);
-    p.V = ctx->V;
-    p.R = g.R;
-    p.logL = log2i(g.R / rpt);
-    p.npad = g.npad;
-    p.spc = ctx->spc_v[run.prec][rclass(g.R)];
-    p.Lx = ctx->dims[0];
-    p.Ly = ctx->dims[1];
-    p.Lz = ctx->dims[2];
-    p.Lt = ctx->dims[3];
-    p.tap = ctx->tap;
-    p.theta = run.theta;
-    p.flags = st.flags | (run.dagger ? mmc::SF_DAGGER : 0);
-    p.err = ctx->step_err;
+  const int rc = rclass(g.R);
+  const bool prof = ctx->prof;
+  // one launch per step; with per-launch profiling events unless the chain is captured
+  auto launch_steps = [&](bool events) -> int {
+    for (size_t k = 0; k < run.steps.size(); ++k) {
+      const Step& st = run.steps[k];
+      mmc::step_params p;
+      std::memset(&p, 0, sizeof(p));
+      p.in = st.in;
+      p.out = st.out;
+      p.aux = st.aux;
+      p.y = run.y;
+      p.codes = run.codes;
+      p.left = run.left;
+      p.coef = reinterpret_cast<const double2*>(dcoef) + k * per;
+      p.partial = run.partial;
+      p.links = run.prec == MMC_F64 ? ctx->links64 : ctx->links32;
+      p.rb_len = run.rb_len;
+      p.nbr = ctx->nbr;
+      p.order = ctx->order_v[run.prec][rc] ? ctx->order : nullptr;
+      p.step = int(k);
+      p.V = ctx->V;
+      p.R = g.R;
+      p.logL = log2i(g.R / rpt);
+      p.npad = g.npad;
+      p.spc = ctx->spc_v[run.prec][rc];
+      p.Lx = ctx->dims[0];
+      p.Ly = ctx->dims[1];
+      p.Lz = ctx->dims[2];
+      p.Lt = ctx->dims[3];
+      p.tap = ctx->tap;
+      p.theta = run.theta;
+      p.flags = st.flags | (run.dagger ? mmc::SF_DAGGER : 0) | (ctx->stream_hints ? mmc::SF_STREAM : 0);
+      p.err = ctx->step_err;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (events) {
+        TRY(prof_event(ctx, &e0));
+        TRY(prof_event(ctx, &e1));
+        CK(cudaEventRecord(e0, s));
+      }
+      bool done = false;
+      if (ctx->var_ver[run.prec][rc] == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+        cudaError_t e3 = cudaSuccess;
+        done = mmc::launch_step3(run.prec, g.R, rpt, run.nbx, ctx->var_ns[run.prec][rc], p, g.nrb, s, &e3);
+        CK(e3);
+      }
+      if (!done && ctx->var_ver[run.prec][rc] >= 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+        cudaError_t e2 = cudaSuccess;
+        const int mb = ctx->var_minb[run.prec][rc];
+        done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, mb, p, g.nrb, s, &e2)
+                                   : mmc::launch_step2_bf16(g.R, rpt, mb, p, g.nrb, s, &e2);
+        CK(e2);
+      }
+      if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec][rc], p, g.nrb, s));
+      if (events) {
+        CK(cudaEventRecord(e1, s));
+        ctx->ev_pending.push_back({e0, e1});
+        if (ctx->ev_pending.size() > 65536) TRY(prof_collect(ctx));
+      }
+    }
+    return MMC_OK;
+  };
+
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cap));
+  if (ctx->use_graphs && run.steps.size() >= 2 && cap == cudaStreamCaptureStatusNone) {
+    // key: everything the launches depend on
+    uint64_t gk = 1469598103934665603ull;
+    auto mix = [&gk](uint64_t v) {
+      for (int b = 0; b < 8; ++b) gk = (gk ^ ((v >> (8 * b)) & 0xff)) * 1099511628211ull;
+    };
+    mix(key);
+    mix(reinterpret_cast<uintptr_t>(dcoef));
+    mix(reinterpret_cast<uintptr_t>(run.y));
+    mix(reinterpret_cast<uintptr_t>(run.codes));
+    mix(reinterpret_cast<uintptr_t>(run.left));
+    mix(reinterpret_cast<uintptr_t>(run.partial));
+    mix(reinterpret_cast<uintptr_t>(run.rb_len));
+    mix(reinterpret_cast<uintptr_t>(run.prec == MMC_F64 ? ctx->links64 : ctx->links32));
+    mix(uint64_t(run.theta) | (uint64_t(run.nbx) << 8) | (uint64_t(run.dagger) << 40) | (uint64_t(run.prec) << 48));
+    mix(uint64_t(g.npad) | (uint64_t(g.R) << 32) | (uint64_t(ctx->stream_hints) << 63));
+    mix(uint64_t(ctx->var_ver[run.prec][rc]) | (uint64_t(rpt) << 8) | (uint64_t(ctx->var_minb[run.prec][rc]) << 16) |
+        (uint64_t(ctx->spc_v[run.prec][rc]) << 24) | (uint64_t(ctx->order_v[run.prec][rc]) << 40) |
+        (uint64_t(ctx->var_ns[run.prec][rc]) << 48));
+    for (const Step& st : run.steps) {
+      mix(reinterpret_cast<uintptr_t>(st.in));
+      mix(reinterpret_cast<uintptr_t>(st.out));
+      mix(reinterpret_cast<uintptr_t>(st.aux));
+      mix(uint64_t(st.flags));
+    }
+    auto it = ctx->graph_cache.find(gk);
+    if (it == ctx->graph_cache.end()) {
+      if (ctx->graph_cache.size() >= 512) {  // bounded
+        CK(cudaStreamSynchronize(s));
+        clear_graphs(ctx);
+      }
+      mmc_ctx::ChainGraph cg;
+      const long long n0 = mmc::launch_count();
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const int rc_launch = launch_steps(false);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+      if (rc_launch != MMC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc_launch;
+      }
+      CK(ce);
+      const cudaError_t ie = cudaGraphInstantiate(&cg.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ie);
+      cg.kernels = int(mmc::launch_count() - n0);
+      mmc::count_launch(-cg.kernels);  // counted when the graph runs
+      it = ctx->graph_cache.emplace(gk, cg).first;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ctx->prof) {
+    if (prof) {
       TRY(prof_event(ctx, &e0));
       TRY(prof_event(ctx, &e1));
       CK(cudaEventRecord(e0, s));
     }
-    bool done = false;
-    const int rc = rclass(g.R);
-    if (ctx->var_ver[run.prec][rc] == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
-      cudaError_t e3 = cudaSuccess;
-      done = mmc::launch_step3(run.prec, g.R, rpt, run.nbx, ctx->var_ns[run.prec][rc], p, g.nrb, s, &e3);
-      CK(e3);
-    }
-    if (!done && ctx->var_ver[run.prec][rc] >= 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
-      cudaError_t e2 = cudaSuccess;
-      const int mb = ctx->var_minb[run.prec][rc];
-      done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, mb, p, g.nrb, s, &e2)
-                                 : mmc::launch_step2_bf16(g.R, rpt, mb, p, g.nrb, s, &e2);
-      CK(e2);
-    }
-    if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec][rc], p, g.nrb, s));
-    if (ctx->prof) {
+    CK(cudaGraphLaunch(it->second.exec, s));
+    mmc::count_launch(it->second.kernels);
+    if (prof) {
       CK(cudaEventRecord(e1, s));
       ctx->ev_pending.push_back({e0, e1});
       if (ctx->ev_pending.size() > 65536) TRY(prof_collect(ctx));
+    }
+  } else {
+    TRY(launch_steps(prof));
+  }
+  for (size_t k = 0; k < run.steps.size(); ++k) {
+    const Step& st = run.steps[k];
+    if (prof) {
       ctx->prof_launches += 1;
       // algorithmic bytes and flops of this launch (all rhs blocks active)
       const double sb = double(elem_bytes(run.prec)) * 12;  // one spinor, one rhs

@@ -107,6 +107,8 @@ _SIGS = {
     "mmc_update_gauge": (_i, [_vp, _dp]),
     "mmc_set_step_variant": (_i, [_vp, _i, _i, _i, _i]),
     "mmc_set_step_variant_class": (_i, [_vp, _i, _i, _i, _i, _i, _i, _i, _i]),
+    "mmc_set_graphs": (_i, [_vp, _i]),
+    "mmc_set_stream_hints": (_i, [_vp, _i]),
     "mmc_set_solve_params": (_i, [_vp, _i, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
     "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
@@ -398,6 +400,14 @@ def mmc_set_solve_params(ctx, m_inner=0, max_outer=0):
 
 def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):
     _check(lib.mmc_set_step_variant(ctx, int(prec), int(rpt), int(minb), int(spc)), ctx)
+
+
+def mmc_set_graphs(ctx, enable):
+    _check(lib.mmc_set_graphs(ctx, int(bool(enable))), ctx)
+
+
+def mmc_set_stream_hints(ctx, enable):
+    _check(lib.mmc_set_stream_hints(ctx, int(bool(enable))), ctx)
 
 
 def mmc_set_step_variant_class(ctx, prec, rhs_class, v):

@@ -253,3 +253,35 @@ def test_step_variant_per_rhs_class(mmc, lat, prec):
         mmc.mmc_set_step_variant(lat.ctx, prec, 1, 102, 0)
         mmc.mmc_set_step_variant(lat.ctx, prec, 0, 4, 0)
         mmc.mmc_set_step_variant(lat.ctx, prec, 0, 300, 0)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_chain_graphs_replay_identical(mmc, lat, prec):
+    """A step chain replayed from its captured CUDA graph gives the same bits as the
+    chain launched degree by degree, for p(M) X and for the level samples; so do the
+    launches without the evict-first hints."""
+    import torch
+    theta = mmc.mmc_leja_order(1.0 + 0.7 * np.exp(2j * np.pi * (np.arange(6) + 0.5) / 6))
+    h = mmc.mmc_poly_from_roots(lat.ctx, theta)
+    h2 = mmc.mmc_poly_from_roots(lat.ctx, theta[:3])
+    nrhs = 19
+    x = mmc.new_field(lat.ctx, nrhs, prec)
+    mmc.mmc_noise(lat.ctx, 2, 0, mmc.MMC_TAG_NOISE, nrhs, prec, x)
+    outs, samples = [], []
+    y = mmc.new_field(lat.ctx, nrhs, prec)  # the same operands: the second call replays the graph
+    try:
+        for on, hints in ((True, True), (True, True), (False, True), (False, False)):  # capture, replay, direct
+            mmc.mmc_set_graphs(lat.ctx, on)
+            mmc.mmc_set_stream_hints(lat.ctx, hints)
+            y.zero_()
+            mmc.mmc_apply_poly(lat.ctx, h, x, y, nrhs, prec)
+            outs.append(y.clone())
+            st = mmc.mmc_trace_level(lat.ctx, h, h2, mmc.MMC_THETA_ONE, 0, nrhs, 40, 3, prec)
+            samples.append(st["samples"])
+        torch.cuda.synchronize()
+        for k in range(1, 4):
+            assert torch.equal(outs[0], outs[k]), k
+            assert np.array_equal(samples[0], samples[k]), k
+    finally:
+        mmc.mmc_set_graphs(lat.ctx, True)
+        mmc.mmc_set_stream_hints(lat.ctx, True)
