@@ -346,6 +346,7 @@ def main():
                      "share_of_step": prof["step_ms"] / ms if ms > 0 else None,
                      "tflops": prof["step_flops"] / (prof["step_ms"] / 1e3) / 1e12 if prof["step_ms"] else 0},
         "gpu_launches": prof["all_launches"],
+        "graphs": {"chain_graph_replays": prof["graph_launches"], "note": mmc.mmc_graph_note(ctx)},
         "launch_index_timed_start": launches_before,
         "e2e": {"value": e2e_val, "unit": "samples/s",
                 "h2d_bytes_per_step": int(U.nbytes),

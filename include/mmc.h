@@ -325,6 +325,7 @@ typedef struct {
   double step_bytes;
   double step_flops;
   long long all_launches;
+  long long graph_launches; /* step chains replayed from a CUDA graph (mmc_set_graphs) */
 } mmc_profile_stats;
 
 /* enable != 0 starts recording (counters reset); 0 stops.  While enabled every
@@ -366,6 +367,9 @@ int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int versio
  * while the caller's stream is already capturing is launched directly into the
  * caller's capture. */
 int mmc_set_graphs(mmc_ctx* ctx, int enable);
+/* "" while chain graphs work; otherwise why the context switched to direct
+ * launches (a capture the driver refused).  Context-owned string. */
+const char* mmc_graph_note(const mmc_ctx* ctx);
 /* enable != 0 (the default): the step kernels read and write the operands that a
  * launch touches once (the result, the auxiliary operand, the accumulator, the
  * left field, the noise codes) with evict-first cache hints, so that L2 keeps the

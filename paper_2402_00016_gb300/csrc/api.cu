@@ -77,6 +77,7 @@ int mmc_destroy(mmc_ctx* ctx) {
     if (b) cudaFree(b);
   prof_collect(ctx);
   clear_graphs(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (auto& kv : ctx->coef_cache) cudaFree(kv.second.p);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -188,6 +189,7 @@ int mmc_profile(mmc_ctx* ctx, int enable) {
     ctx->prof_launches = 0;
     ctx->prof_ms = ctx->prof_bytes = ctx->prof_flops = 0;
     ctx->launches0 = mmc::launch_count();
+    ctx->graph_launches0 = ctx->graph_launches;
   }
   ctx->prof = enable != 0;
   return MMC_OK;
@@ -203,6 +205,7 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out) {
   out->step_bytes = ctx->prof_bytes;
   out->step_flops = ctx->prof_flops;
   out->all_launches = mmc::launch_count() - ctx->launches0;
+  out->graph_launches = ctx->graph_launches - ctx->graph_launches0;
   return MMC_OK;
 }
 
@@ -247,8 +250,11 @@ int mmc_set_graphs(mmc_ctx* ctx, int enable) {
     clear_graphs(ctx);
   }
   ctx->use_graphs = enable != 0;
+  if (enable) ctx->graph_note.clear();
   return MMC_OK;
 }
+
+const char* mmc_graph_note(const mmc_ctx* ctx) { return ctx ? ctx->graph_note.c_str() : ""; }
 
 int mmc_set_stream_hints(mmc_ctx* ctx, int enable) {
   if (!ctx) return MMC_ERR_ARG;

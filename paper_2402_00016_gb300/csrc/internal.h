@@ -83,6 +83,10 @@ struct mmc_ctx {
   };
   std::map<uint64_t, ChainGraph> graph_cache;
   bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;  // private non-blocking stream the graphs are captured on
+  long long graph_launches = 0;       // chains run as graph replays
+  long long graph_launches0 = 0;      // value at the last mmc_profile(ctx, 1)
+  std::string graph_note;             // why graphs were switched off, if they were
   bool stream_hints = true;  // evict-first hints on once-touched step operands (SF_STREAM)
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
@@ -290,7 +294,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
   const int rc = rclass(g.R);
   const bool prof = ctx->prof;
   // one launch per step; with per-launch profiling events unless the chain is captured
-  auto launch_steps = [&](bool events) -> int {
+  auto launch_steps = [&](bool events, cudaStream_t s) -> int {
     for (size_t k = 0; k < run.steps.size(); ++k) {
       const Step& st = run.steps[k];
       mmc::step_params p;
@@ -352,6 +356,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
 
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(s, &cap));
+  mmc_ctx::ChainGraph* cgp = nullptr;  // the graph to replay, if any
   if (ctx->use_graphs && run.steps.size() >= 2 && cap == cudaStreamCaptureStatusNone) {
     // key: everything the launches depend on
     uint64_t gk = 1469598103934665603ull;
@@ -383,40 +388,53 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
         CK(cudaStreamSynchronize(s));
         clear_graphs(ctx);
       }
+      // captured on the context's private non-blocking stream (a blocking stream is
+      // tied to the legacy default stream), replayed on s
+      if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
       mmc_ctx::ChainGraph cg;
+      bool built = false;
       const long long n0 = mmc::launch_count();
-      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      const int rc_launch = launch_steps(false);
-      cudaGraph_t graph = nullptr;
-      const cudaError_t ce = cudaStreamEndCapture(s, &graph);
-      if (rc_launch != MMC_OK) {
+      cudaError_t be = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (be == cudaSuccess) {
+        const int rc_launch = launch_steps(false, ctx->cap_stream);
+        cudaGraph_t graph = nullptr;
+        be = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (rc_launch == MMC_OK && be == cudaSuccess && graph) be = cudaGraphInstantiate(&cg.exec, graph, 0);
+        built = rc_launch == MMC_OK && be == cudaSuccess && cg.exec;
         if (graph) cudaGraphDestroy(graph);
-        return rc_launch;
       }
-      CK(ce);
-      const cudaError_t ie = cudaGraphInstantiate(&cg.exec, graph, 0);
-      cudaGraphDestroy(graph);
-      CK(ie);
-      cg.kernels = int(mmc::launch_count() - n0);
-      mmc::count_launch(-cg.kernels);  // counted when the graph runs
-      it = ctx->graph_cache.emplace(gk, cg).first;
+      mmc::count_launch(-int(mmc::launch_count() - n0));  // counted when the graph (or the fallback) runs
+      if (built) {
+        cg.kernels = int(run.steps.size());
+        cgp = &ctx->graph_cache.emplace(gk, cg).first->second;
+      } else {
+        // capture refused: launch directly from now on and keep the reason
+        cudaGetLastError();
+        if (cg.exec) cudaGraphExecDestroy(cg.exec);
+        ctx->use_graphs = false;
+        ctx->graph_note = std::string("graph capture failed, direct launches: ") + cudaGetErrorString(be);
+      }
+    } else {
+      cgp = &it->second;
     }
+  }
+  if (cgp) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (prof) {
       TRY(prof_event(ctx, &e0));
       TRY(prof_event(ctx, &e1));
       CK(cudaEventRecord(e0, s));
     }
-    CK(cudaGraphLaunch(it->second.exec, s));
-    mmc::count_launch(it->second.kernels);
+    CK(cudaGraphLaunch(cgp->exec, s));
+    mmc::count_launch(cgp->kernels);
+    ctx->graph_launches += 1;
     if (prof) {
       CK(cudaEventRecord(e1, s));
       ctx->ev_pending.push_back({e0, e1});
       if (ctx->ev_pending.size() > 65536) TRY(prof_collect(ctx));
     }
-  } else {
-    TRY(launch_steps(prof));
   }
+  if (!cgp) TRY(launch_steps(prof, s));
   for (size_t k = 0; k < run.steps.size(); ++k) {
     const Step& st = run.steps[k];
     if (prof) {

@@ -273,11 +273,15 @@ def test_chain_graphs_replay_identical(mmc, lat, prec):
         for on, hints in ((True, True), (True, True), (False, True), (False, False)):  # capture, replay, direct
             mmc.mmc_set_graphs(lat.ctx, on)
             mmc.mmc_set_stream_hints(lat.ctx, hints)
+            mmc.mmc_profile(lat.ctx, 1)
             y.zero_()
             mmc.mmc_apply_poly(lat.ctx, h, x, y, nrhs, prec)
             outs.append(y.clone())
             st = mmc.mmc_trace_level(lat.ctx, h, h2, mmc.MMC_THETA_ONE, 0, nrhs, 40, 3, prec)
             samples.append(st["samples"])
+            replays = mmc.mmc_profile_read(lat.ctx)["graph_launches"]
+            mmc.mmc_profile(lat.ctx, 0)
+            assert (replays > 0) == on, (on, replays, mmc.mmc_graph_note(lat.ctx))
         torch.cuda.synchronize()
         for k in range(1, 4):
             assert torch.equal(outs[0], outs[k]), k
