@@ -326,6 +326,7 @@ typedef struct {
   double step_flops;
   long long all_launches;
   long long graph_launches; /* step chains replayed from a CUDA graph (mmc_set_graphs) */
+  long long graph_captures; /* of which captured (and instantiated) first */
 } mmc_profile_stats;
 
 /* enable != 0 starts recording (counters reset); 0 stops.  While enabled every
@@ -370,12 +371,6 @@ int mmc_set_graphs(mmc_ctx* ctx, int enable);
 /* "" while chain graphs work; otherwise why the context switched to direct
  * launches (a capture the driver refused).  Context-owned string. */
 const char* mmc_graph_note(const mmc_ctx* ctx);
-/* enable != 0 (the default): the step kernels read and write the operands that a
- * launch touches once (the result, the auxiliary operand, the accumulator, the
- * left field, the noise codes) with evict-first cache hints, so that L2 keeps the
- * iterate, each element of which is read by nine sites.  Results are identical
- * either way. */
-int mmc_set_stream_hints(mmc_ctx* ctx, int enable);
 /* Autotuner: time every step-kernel variant on an nrhs-vector field of
  * precision prec (random data, CUDA events, median of 3 after a warm-up),
  * keep the fastest for that precision and the rhs-block class of nrhs and

@@ -190,6 +190,7 @@ int mmc_profile(mmc_ctx* ctx, int enable) {
     ctx->prof_ms = ctx->prof_bytes = ctx->prof_flops = 0;
     ctx->launches0 = mmc::launch_count();
     ctx->graph_launches0 = ctx->graph_launches;
+    ctx->graph_captures0 = ctx->graph_captures;
   }
   ctx->prof = enable != 0;
   return MMC_OK;
@@ -206,6 +207,7 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out) {
   out->step_flops = ctx->prof_flops;
   out->all_launches = mmc::launch_count() - ctx->launches0;
   out->graph_launches = ctx->graph_launches - ctx->graph_launches0;
+  out->graph_captures = ctx->graph_captures - ctx->graph_captures0;
   return MMC_OK;
 }
 
@@ -255,12 +257,6 @@ int mmc_set_graphs(mmc_ctx* ctx, int enable) {
 }
 
 const char* mmc_graph_note(const mmc_ctx* ctx) { return ctx ? ctx->graph_note.c_str() : ""; }
-
-int mmc_set_stream_hints(mmc_ctx* ctx, int enable) {
-  if (!ctx) return MMC_ERR_ARG;
-  ctx->stream_hints = enable != 0;
-  return MMC_OK;
-}
 
 int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int version, int rpt, int minb, int spc,
                                int blocked, int ns) {

@@ -15,8 +15,7 @@ enum StepFlags : int {
   SF_BIL_CODES = 16, // bilinear with Z(4) noise given by packed codes
   SF_BIL_LEFT = 32,  // bilinear with an explicit left field
   SF_BIL_OUT = 64,   // bilinear also of `out` (weight w_out)
-  SF_DAGGER = 128,   // use M^+ (gamma_mu signs flipped)
-  SF_STREAM = 256    // once-touched operands (result, aux, accumulator, codes) with evict-first hints
+  SF_DAGGER = 128    // use M^+ (gamma_mu signs flipped)
 };
 
 // Per-step parameters.  Fields use the blocked layout [rb][site][c][R].

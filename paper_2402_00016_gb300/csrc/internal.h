@@ -86,8 +86,8 @@ struct mmc_ctx {
   cudaStream_t cap_stream = nullptr;  // private non-blocking stream the graphs are captured on
   long long graph_launches = 0;       // chains run as graph replays
   long long graph_launches0 = 0;      // value at the last mmc_profile(ctx, 1)
+  long long graph_captures = 0, graph_captures0 = 0;
   std::string graph_note;             // why graphs were switched off, if they were
-  bool stream_hints = true;  // evict-first hints on once-touched step operands (SF_STREAM)
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
   std::string err;
@@ -323,7 +323,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       p.Lt = ctx->dims[3];
       p.tap = ctx->tap;
       p.theta = run.theta;
-      p.flags = st.flags | (run.dagger ? mmc::SF_DAGGER : 0) | (ctx->stream_hints ? mmc::SF_STREAM : 0);
+      p.flags = st.flags | (run.dagger ? mmc::SF_DAGGER : 0);
       p.err = ctx->step_err;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (events) {
@@ -372,7 +372,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     mix(reinterpret_cast<uintptr_t>(run.rb_len));
     mix(reinterpret_cast<uintptr_t>(run.prec == MMC_F64 ? ctx->links64 : ctx->links32));
     mix(uint64_t(run.theta) | (uint64_t(run.nbx) << 8) | (uint64_t(run.dagger) << 40) | (uint64_t(run.prec) << 48));
-    mix(uint64_t(g.npad) | (uint64_t(g.R) << 32) | (uint64_t(ctx->stream_hints) << 63));
+    mix(uint64_t(g.npad) | (uint64_t(g.R) << 32));
     mix(uint64_t(ctx->var_ver[run.prec][rc]) | (uint64_t(rpt) << 8) | (uint64_t(ctx->var_minb[run.prec][rc]) << 16) |
         (uint64_t(ctx->spc_v[run.prec][rc]) << 24) | (uint64_t(ctx->order_v[run.prec][rc]) << 40) |
         (uint64_t(ctx->var_ns[run.prec][rc]) << 48));
@@ -407,6 +407,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       if (built) {
         cg.kernels = int(run.steps.size());
         cgp = &ctx->graph_cache.emplace(gk, cg).first->second;
+        ctx->graph_captures += 1;
       } else {
         // capture refused: launch directly from now on and keep the reason
         cudaGetLastError();

@@ -29,7 +29,6 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
   const size_t rb_off = size_t(rb) * p.V * 12 * R;
   const S* in = reinterpret_cast<const S*>(p.in) + rb_off + r0;
   const bool bil_out = (p.flags & SF_BIL_OUT) != 0;
-  const bool cs = (p.flags & SF_STREAM) != 0;
 
   cx<T> ca[RPT], cb[RPT], cg[RPT], cwi[RPT], cwo[RPT];
 #pragma unroll
@@ -90,7 +89,7 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
     uint32_t code[RPT];
     if (ACC == ACC_CODES) {
 #pragma unroll
-      for (int j = 0; j < RPT; ++j) code[j] = load_code(cs, p.codes + (size_t(rb) * p.V + site) * R + r0 + j);
+      for (int j = 0; j < RPT; ++j) code[j] = __ldg(p.codes + (size_t(rb) * p.V + site) * R + r0 + j);
     }
     cx<T> si[RPT], so[RPT];
 #pragma unroll
@@ -103,20 +102,20 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
       for (int j = 0; j < RPT; ++j) vout[j] = cfma(cb[j], acc[c][j], cmul(ca[j], vin[j]));
       if (AUX) {
         cx<T> ax[RPT];
-        load_once<S, RPT>(cs, reinterpret_cast<const S*>(p.aux) + boff + c * R, ax);
+        load_rpt<S, RPT>(reinterpret_cast<const S*>(p.aux) + boff + c * R, ax);
 #pragma unroll
         for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], ax[j], vout[j]);
       }
-      store_out<S, RPT>(cs, reinterpret_cast<S*>(p.out) + boff + c * R, vout);
+      store_rpt<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout);
       if (ACC == ACC_Y) {
         float2* yp = reinterpret_cast<float2*>(p.y) + boff + c * R;
 #pragma unroll
         for (int j = 0; j < RPT; ++j) {
-          float2 yv = load_y(cs, yp + j);
+          float2 yv = yp[j];
           cx<T> a = cmake(yv.x, yv.y);
           a = cfma(cwi[j], vin[j], a);
           if (bil_out) a = cfma(cwo[j], vout[j], a);
-          store_y(cs, yp + j, make_float2(a.re, a.im));
+          yp[j] = make_float2(a.re, a.im);
         }
       }
       if (BIL) {
@@ -139,7 +138,7 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
           }
         } else {
           cx<T> eta[RPT];
-          load_once<S, RPT>(cs, reinterpret_cast<const S*>(p.left) + boff + size_t(cp) * R, eta);
+          load_rpt<S, RPT>(reinterpret_cast<const S*>(p.left) + boff + size_t(cp) * R, eta);
 #pragma unroll
           for (int j = 0; j < RPT; ++j) {
             si[j] = cfmac(eta[j], cscale(vin[j], sg), si[j]);

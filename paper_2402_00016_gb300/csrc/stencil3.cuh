@@ -297,7 +297,6 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
   const int xs = lane_ok ? sx : 0;
   const int warp = tid >> 5, lane = tid & 31;
   const bool bil_out = (p.flags & SF_BIL_OUT) != 0;
-  const bool cs = (p.flags & SF_STREAM) != 0;
   cx<float> ca[RPT], cb[RPT], cg[RPT], cwi[RPT], cwo[RPT];
   int cur_rb = -1;
   double bre[RPT], bim[RPT];
@@ -359,12 +358,12 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
     uint32_t code[RPT];
     if (ACC == ACC_CODES) {
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) code[q] = lane_ok ? load_code(cs, p.codes + (size_t(rb) * p.V + site) * R + r0 + q) : 0u;
+      for (int q = 0; q < RPT; ++q) code[q] = lane_ok ? __ldg(p.codes + (size_t(rb) * p.V + site) * R + r0 + q) : 0u;
     }
     cx<float> ax[12][RPT];
     if (AUX) {
 #pragma unroll
-      for (int c = 0; c < 12; ++c) load_once<S, RPT>(cs, reinterpret_cast<const S*>(p.aux) + fofs + c * R, ax[c]);
+      for (int c = 0; c < 12; ++c) load_rpt<S, RPT>(reinterpret_cast<const S*>(p.aux) + fofs + c * R, ax[c]);
     }
     cx<float> acc[12][RPT];
 #pragma unroll
@@ -425,16 +424,16 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
           vout[q] = cfma(cb[q], acc[c][q], cmul(ca[q], vin[q]));
           if (AUX) vout[q] = cfma(cg[q], ax[c][q], vout[q]);
         }
-        store_out<S, RPT>(cs, reinterpret_cast<S*>(p.out) + fofs + c * R, vout);
+        store_rpt<S, RPT>(reinterpret_cast<S*>(p.out) + fofs + c * R, vout);
         if (ACC == ACC_Y) {
           float2* yp = reinterpret_cast<float2*>(p.y) + fofs + c * R;
 #pragma unroll
           for (int q = 0; q < RPT; ++q) {
-            const float2 yv = load_y(cs, yp + q);
+            const float2 yv = yp[q];
             cx<float> a = cmake(yv.x, yv.y);
             a = cfma(cwi[q], vin[q], a);
             if (bil_out) a = cfma(cwo[q], vout[q], a);
-            store_y(cs, yp + q, make_float2(a.re, a.im));
+            yp[q] = make_float2(a.re, a.im);
           }
         }
         if (BIL) {
@@ -456,7 +455,7 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
             }
           } else {
             cx<float> eta[RPT];
-            load_once<S, RPT>(cs, reinterpret_cast<const S*>(p.left) + fofs + size_t(cp) * R, eta);
+            load_rpt<S, RPT>(reinterpret_cast<const S*>(p.left) + fofs + size_t(cp) * R, eta);
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
               si[q] = cfmac(eta[q], cscale(vin[q], sg), si[q]);

@@ -101,72 +101,6 @@ __device__ __forceinline__ void store_rpt(S* p, const cx<typename StoreTraits<S>
   }
 }
 
-// Streaming forms (ld.global.cs / st.global.cs: lines allocated evict-first) for the
-// operands one launch touches once -- the result, the auxiliary operand, the
-// accumulator, the left field.  Every element of the iterate is read by nine sites
-// (its own and eight neighbours') within a window of two t-slices; keeping the
-// once-touched data from displacing it lets L2 serve those re-reads.
-template <typename S, int RPT>
-__device__ __forceinline__ void store_rpt_cs(S* p, const cx<typename StoreTraits<S>::R> (&v)[RPT]) {
-  S tmp[RPT];
-#pragma unroll
-  for (int j = 0; j < RPT; ++j) from_cx(v[j], tmp[j]);
-  if constexpr (sizeof(S) * RPT == 16) {
-    __stcs(reinterpret_cast<uint4*>(p), *reinterpret_cast<const uint4*>(tmp));
-  } else if constexpr (sizeof(S) * RPT == 8) {
-    __stcs(reinterpret_cast<uint2*>(p), *reinterpret_cast<const uint2*>(tmp));
-  } else if constexpr (sizeof(S) * RPT == 4) {
-    __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(tmp));
-  } else {
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) __stcs(reinterpret_cast<uint4*>(p + j), *reinterpret_cast<const uint4*>(&tmp[j]));
-  }
-}
-
-template <typename S, int RPT>
-__device__ __forceinline__ void load_rpt_cs(const S* p, cx<typename StoreTraits<S>::R> (&v)[RPT]) {
-  if constexpr (sizeof(S) * RPT == 16) {
-    const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(p));
-    const S* s = reinterpret_cast<const S*>(&raw);
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) v[j] = to_cx(s[j]);
-  } else if constexpr (sizeof(S) * RPT == 8) {
-    const uint2 raw = __ldcs(reinterpret_cast<const uint2*>(p));
-    const S* s = reinterpret_cast<const S*>(&raw);
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) v[j] = to_cx(s[j]);
-  } else if constexpr (sizeof(S) * RPT == 4) {
-    const unsigned int raw = __ldcs(reinterpret_cast<const unsigned int*>(p));
-    const S* s = reinterpret_cast<const S*>(&raw);
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) v[j] = to_cx(s[j]);
-  } else {
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-      const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(p + j));
-      v[j] = to_cx(*reinterpret_cast<const S*>(&raw));
-    }
-  }
-}
-
-// result store and once-read loads, streaming when the launch asks for it
-template <typename S, int RPT>
-__device__ __forceinline__ void store_out(bool cs, S* p, const cx<typename StoreTraits<S>::R> (&v)[RPT]) {
-  if (cs) store_rpt_cs<S, RPT>(p, v);
-  else store_rpt<S, RPT>(p, v);
-}
-template <typename S, int RPT>
-__device__ __forceinline__ void load_once(bool cs, const S* p, cx<typename StoreTraits<S>::R> (&v)[RPT]) {
-  if (cs) load_rpt_cs<S, RPT>(p, v);
-  else load_rpt<S, RPT>(p, v);
-}
-__device__ __forceinline__ uint32_t load_code(bool cs, const uint32_t* p) { return cs ? __ldcs(p) : __ldg(p); }
-__device__ __forceinline__ float2 load_y(bool cs, const float2* p) { return cs ? __ldcs(p) : *p; }
-__device__ __forceinline__ void store_y(bool cs, float2* p, float2 v) {
-  if (cs) __stcs(p, v);
-  else *p = v;
-}
-
 // ------------------------------------------------------------ complex ops
 template <typename T>
 __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return cmake(a.re + b.re, a.im + b.im); }

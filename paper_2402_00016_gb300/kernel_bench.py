@@ -29,7 +29,6 @@ def main(argv=None):
     ap.add_argument("--blocked", type=int, default=-1, help="1: 4D-blocked site traversal, 0: lexicographic")
     ap.add_argument("--ns", type=int, default=-1, help="ring slots of the staged kernel (0: as many as fit)")
     ap.add_argument("--autotune", action="store_true", help="pick the kernel variant with mmc_autotune first")
-    ap.add_argument("--stream-hints", type=int, default=1, help="evict-first hints on once-touched operands")
     ap.add_argument("--graphs", type=int, default=1, help="replay step chains as CUDA graphs")
     ap.add_argument("--deflate", type=int, default=0,
                     help="k > 0: random deflation space of k vectors, levels deflated (tensor-core projections)")
@@ -44,7 +43,6 @@ def main(argv=None):
     try:
         mmc.mmc_load_gauge(ctx, synth.random_gauge(a.dims, 0.25, 1), 0.1565, 1)
         mmc.mmc_set_step_variant(ctx, prec, a.rpt, a.minb, a.spc)
-        mmc.mmc_set_stream_hints(ctx, a.stream_hints)
         mmc.mmc_set_graphs(ctx, a.graphs)
         if a.blocked >= 0:
             mmc.mmc_set_step_variant(ctx, prec, 0, 200 + a.blocked, 0)
@@ -75,7 +73,7 @@ def main(argv=None):
         p = mmc.mmc_profile_read(ctx)
         vol = int(np.prod(a.dims))
         out = {"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "degree": a.degree,
-               "stream_hints": a.stream_hints, "graphs": a.graphs,
+               "graphs": a.graphs,
                "step_launches": p["step_launches"], "avg_launch_ms": p["step_ms"] / max(1, p["step_launches"]),
                "algorithmic_GBps": p["step_bytes"] / p["step_ms"] / 1e6 if p["step_ms"] else 0,
                "TFLOPs": p["step_flops"] / p["step_ms"] / 1e9 if p["step_ms"] else 0,

@@ -60,7 +60,8 @@ MMC_ALLOC_EQUAL, MMC_ALLOC_COST = 0, 1
 
 class mmc_profile_stats(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_longlong), ("step_ms", _d), ("step_bytes", _d), ("step_flops", _d),
-                ("all_launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong)]
+                ("all_launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong),
+                ("graph_captures", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -108,7 +109,6 @@ _SIGS = {
     "mmc_set_step_variant": (_i, [_vp, _i, _i, _i, _i]),
     "mmc_set_step_variant_class": (_i, [_vp, _i, _i, _i, _i, _i, _i, _i, _i]),
     "mmc_set_graphs": (_i, [_vp, _i]),
-    "mmc_set_stream_hints": (_i, [_vp, _i]),
     "mmc_graph_note": (ctypes.c_char_p, [_vp]),
     "mmc_set_solve_params": (_i, [_vp, _i, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
@@ -409,10 +409,6 @@ def mmc_set_graphs(ctx, enable):
 
 def mmc_graph_note(ctx):
     return lib.mmc_graph_note(ctx).decode()
-
-
-def mmc_set_stream_hints(ctx, enable):
-    _check(lib.mmc_set_stream_hints(ctx, int(bool(enable))), ctx)
 
 
 def mmc_set_step_variant_class(ctx, prec, rhs_class, v):
