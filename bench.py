@@ -160,6 +160,9 @@ def main():
     ap.add_argument("--precond", default="in", choices=["in", "dbl"],
                     help="right preconditioner of those solves: the inner GMRES polynomial (degree 39) or the "
                          "double polynomial (degree 319)")
+    ap.add_argument("--solve-storage", default="f32", choices=["f32", "bf16"],
+                    help="storage of the inner FGMRES stage and its preconditioner chain in those solves (the "
+                         "FP64 outer loop refines to 1e-10 either way)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
                     help="spinor storage of the polynomial chains (BF16 rounding shifts the level samples by "
                          "several standard errors on this workload: see error_vs_fp64)")
@@ -219,6 +222,7 @@ def main():
             with open(args.tune_file, "w") as f:
                 json.dump(tune, f)
     mmc.mmc_set_solve_params(ctx, args.solve_m, 400)
+    mmc.mmc_set_solve_storage(ctx, mmc.PREC[args.solve_storage])
     t_poly = time.time() - t_setup
     lam = mmc.mmc_deflate(ctx, args.deflate_k, h["in"], args.arnoldi, 1e-3) if args.deflate_k > 0 else []
     pre = h[args.precond]
@@ -337,7 +341,7 @@ def main():
                    "noises": [8, 32, 128, 512], "storage": args.storage, "arithmetic": "fp32, fp64 bilinears",
                    "deflated": len(lam), "probe_colours": ncol,
                    "solves": {"fgmres_m": args.solve_m, "precond": "p_in (degree 39)" if args.precond == "in"
-                              else "p_dbl (degree 319)", "tol": 1e-10}, "l2": "inputs larger than L2 (GB-sized fields)",
+                              else "p_dbl (degree 319)", "tol": 1e-10, "inner_storage": args.solve_storage}, "l2": "inputs larger than L2 (GB-sized fields)",
                    "parallelism": "replicas" if world > 1 else "1 gpu"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "step_kernel (fused stencil + Leja step)",

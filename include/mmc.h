@@ -338,6 +338,13 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out);
 /* Inner FGMRES length and outer-cycle limit of the solves inside mmc_trace_level
  * (defaults 48 and 400).  Values <= 0 keep the current setting. */
 int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
+/* Storage of the inner FGMRES stage (its preconditioner chain included) in the
+ * solves of the M^-1 level of a reduced-precision mmc_trace_level (the
+ * prec_inner of mmc_solve): MMC_F32 (default) or MMC_BF16.  The FP64 outer loop
+ * still refines every solve to a relative residual of 1e-10, so the level's
+ * samples differ only within that tolerance; a flexible inner iteration absorbs
+ * the BF16 rounding of the preconditioner.  MMC_ERR_ARG for any other value. */
+int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner);
 
 /* Launch variant of the fused step kernel for precision prec, for both rhs-block
  * classes (R < 16 and R = 16; mmc_set_step_variant_class sets one): rpt right-hand

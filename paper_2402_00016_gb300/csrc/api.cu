@@ -218,6 +218,13 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer) {
   return MMC_OK;
 }
 
+int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner) {
+  if (!ctx) return MMC_ERR_ARG;
+  if (prec_inner != MMC_F32 && prec_inner != MMC_BF16) RET(MMC_ERR_ARG, "mmc_set_solve_storage: MMC_F32 or MMC_BF16");
+  ctx->solve_inner = prec_inner;
+  return MMC_OK;
+}
+
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
   if (!ctx || prec < 0 || prec > 2) return MMC_ERR_ARG;
   if (minb >= 300) {  // minb = 300 + n: ring slots of the staged kernel (0: as many as fit)

@@ -90,6 +90,7 @@ struct mmc_ctx {
   std::string graph_note;             // why graphs were switched off, if they were
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
+  int solve_inner = MMC_F32;  // inner FGMRES storage of the reduced-precision levels' solves (F32 or BF16)
   std::string err;
   long long matvecs = 0;
   int spc_v[3][2] = {{64, 64}, {64, 64}, {64, 64}};  // sites per CTA of the step kernel (per variant class)

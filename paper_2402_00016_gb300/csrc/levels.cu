@@ -670,7 +670,7 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     std::vector<double> rel;
     int its = 0;
     // the plain FP64 form (prec = MMC_F64) solves in FP64 throughout; otherwise FP32 inner
-    TRY(solve_impl(ctx, b64, x64, n_noise, 1e-10, precond, prec == MMC_F64 ? MMC_F64 : MMC_F32, ctx->solve_m,
+    TRY(solve_impl(ctx, b64, x64, n_noise, 1e-10, precond, prec == MMC_F64 ? MMC_F64 : ctx->solve_inner, ctx->solve_m,
                    ctx->solve_max_outer, &its, rel, s));
     if (y64) {  // y <- x - y
       std::vector<cd> one(g.npad, cd(1, 0)), minus(g.npad, cd(-1, 0));

@@ -126,21 +126,31 @@ def test_solve_refined(mmc, lat):
             assert rel[j] <= 1e-10
 
 
-def test_level_inverse_vs_dense(mmc):
-    """Tr(M^-1 - p) samples on the 4^4 plain workload (eps 0.5, kappa 0.12) vs a dense solve."""
+@pytest.mark.parametrize("prec,inner", [(0, 1), (1, 1), (1, 2)])
+def test_level_inverse_vs_dense(mmc, prec, inner):
+    """Tr(M^-1 - p) samples on the 4^4 plain workload (eps 0.5, kappa 0.12) vs a dense solve:
+    the FP64 form, and the FP32 form with its solves' inner stage (preconditioner chain
+    included) stored in FP32 or BF16, all refined to the same 1e-10 residual."""
     L = Lat(mmc, (4, 4, 4, 4), 0.5, 0.12, seed=0)
     try:
         A = wilson.dense_M(L.U, L.kappa)
         h, th = mmc.mmc_gmres_poly(L.ctx, 16)
         n = 6
-        st = mmc.mmc_trace_level(L.ctx, mmc.MMC_INV, h, mmc.MMC_THETA_ONE, 0, n, 0, 0, mmc.MMC_F64)
+        mmc.mmc_set_solve_storage(L.ctx, inner)
+        st = mmc.mmc_trace_level(L.ctx, mmc.MMC_INV, h, mmc.MMC_THETA_ONE, 0, n, 0, 0, prec, precond=h)
         for j in range(n):
             e = L.eta(j, 0)
             xinv = np.linalg.solve(A, e)
-            want = np.vdot(e, xinv) - np.vdot(e, krylov.apply_poly(L.op, th, e))
-            # solve to 1e-10 relative residual: |delta x| <= ||A^-1|| 1e-10 ||e||
+            pe = krylov.apply_poly(L.op, th, e)
+            want = np.vdot(e, xinv) - np.vdot(e, pe)
+            # solve to 1e-10 relative residual: |delta x| <= ||A^-1|| 1e-10 ||e||; the FP32
+            # subtracted operand p(M) e adds at most 1e-5 ||e|| ||p(M) e|| (Cauchy-Schwarz)
             bound = np.linalg.norm(e) ** 2 * 1e-10 * 10
+            if prec != 0:
+                bound += 1e-5 * np.linalg.norm(e) * np.linalg.norm(pe)
             assert abs(st["samples"][j] - want) < bound
+        with pytest.raises(mmc.MMCError):
+            mmc.mmc_set_solve_storage(L.ctx, 0)
     finally:
         mmc.mmc_destroy(L.ctx)
 
