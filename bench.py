@@ -156,7 +156,7 @@ def main():
     ap.add_argument("--impl", default="mmc")
     ap.add_argument("--deflate-k", type=int, default=100)
     ap.add_argument("--arnoldi", type=int, default=200)
-    ap.add_argument("--solve-m", type=int, default=16, help="inner FGMRES length of the M^-1 level solves")
+    ap.add_argument("--solve-m", type=int, default=8, help="inner FGMRES length of the M^-1 level solves")
     ap.add_argument("--precond", default="in", choices=["in", "dbl"],
                     help="right preconditioner of those solves: the inner GMRES polynomial (degree 39) or the "
                          "double polynomial (degree 319)")
