@@ -105,6 +105,9 @@ def level_plan(h):
 # matvecs per sample of the polynomial parts (solves excluded) -- used to scale the CPU legs
 POLY_MATVECS = 8 * 319 + 32 * (319 + 128) + 128 * (128 + 32) + 512 * (32 + 8)
 SAMPLES = 8 + 32 + 128 + 512
+# DRAM traffic / algorithmic bytes of the level-chain step kernel, measured by ncu on 24^4 with
+# 64 right-hand sides (6.704 GB of dram__bytes_read+write against 4.544 GB algorithmic)
+TRAFFIC_RATIO = 6.704 / 4.544
 
 
 def oracle_slice(U, kappa, dims, reps):
@@ -331,6 +334,7 @@ def main():
                          "oracle)" % (args.cpu_reps, mv, dt, POLY_MATVECS / SAMPLES)}
 
     peak, peak_kind = measured_peaks()
+    avg_bytes = prof["step_bytes"] / max(1, prof["step_launches"])
     achieved = prof["step_bytes"] / (prof["step_ms"] / 1e3) / 1e9 if prof["step_ms"] > 0 else 0.0
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
@@ -344,7 +348,12 @@ def main():
                               else "p_dbl (degree 319)", "tol": 1e-10, "inner_storage": args.solve_storage}, "l2": "inputs larger than L2 (GB-sized fields)",
                    "parallelism": "replicas" if world > 1 else "1 gpu"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "step_kernel (fused stencil + Leja step)",
+                     "frac": achieved / peak, "traffic": avg_bytes * TRAFFIC_RATIO,
+                     "traffic_basis": "DRAM bytes per average step launch: its algorithmic bytes x %.3f, the "
+                                      "dram__bytes_read+write / algorithmic ratio of one ncu capture of the "
+                                      "level-chain step kernel (FP32, 16-rhs blocks, 24^4, 64 rhs; "
+                                      "profiles/step2_kernel_f32_codes_24x24x24x24_64rhs.md)" % TRAFFIC_RATIO,
+                     "kernel": "step_kernel (fused stencil + Leja step)",
                      "peak_kind": peak_kind, "launches": prof["step_launches"],
                      "avg_launch_ms": prof["step_ms"] / max(1, prof["step_launches"]),
                      "share_of_step": prof["step_ms"] / ms if ms > 0 else None,
