@@ -345,6 +345,13 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
  * samples differ only within that tolerance; a flexible inner iteration absorbs
  * the BF16 rounding of the preconditioner.  MMC_ERR_ARG for any other value. */
 int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner);
+/* Largest right-hand-side block R of the blocked field layout [rb][site][c][R]
+ * (8 or 16, default 16).  A batch of N vectors uses R = min(rmax, next power of
+ * two >= N).  It changes the layout of every field sized or interpreted after
+ * the call (mmc_field_bytes, mmc_pack, mmc_unpack), so set it before creating
+ * fields; smaller blocks halve the L2 footprint of a site at the price of more
+ * link reads per vector.  MMC_ERR_ARG for other values. */
+int mmc_set_rhs_block_max(mmc_ctx* ctx, int rmax);
 
 /* Launch variant of the fused step kernel for precision prec, for both rhs-block
  * classes (R < 16 and R = 16; mmc_set_step_variant_class sets one): rpt right-hand

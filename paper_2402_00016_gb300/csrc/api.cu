@@ -218,6 +218,13 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer) {
   return MMC_OK;
 }
 
+int mmc_set_rhs_block_max(mmc_ctx* ctx, int rmax) {
+  if (!ctx) return MMC_ERR_ARG;
+  if (rmax != 8 && rmax != 16) RET(MMC_ERR_ARG, "mmc_set_rhs_block_max: 8 or 16");
+  ctx->rhs_max = rmax;
+  return MMC_OK;
+}
+
 int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner) {
   if (!ctx) return MMC_ERR_ARG;
   if (prec_inner != MMC_F32 && prec_inner != MMC_BF16) RET(MMC_ERR_ARG, "mmc_set_solve_storage: MMC_F32 or MMC_BF16");

@@ -90,6 +90,7 @@ struct mmc_ctx {
   std::string graph_note;             // why graphs were switched off, if they were
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
+  int rhs_max = 16;           // largest rhs block R of the blocked field layout (8 or 16)
   int solve_inner = MMC_F32;  // inner FGMRES storage of the reduced-precision levels' solves (F32 or BF16)
   std::string err;
   long long matvecs = 0;
@@ -141,16 +142,16 @@ using mmc::geom;
 
 inline size_t elem_bytes(int prec) { return prec == MMC_F64 ? 16 : (prec == MMC_F32 ? 8 : 4); }
 
-inline int rhs_block(int nrhs) {
+inline int rhs_block(int nrhs, int rmax = 16) {
   int R = 1;
-  while (R < nrhs && R < 16) R <<= 1;
+  while (R < nrhs && R < rmax) R <<= 1;
   return R;
 }
 
 inline geom make_geom(const mmc_ctx* ctx, int nrhs) {
   geom g;
   g.V = ctx->V;
-  g.R = rhs_block(nrhs);
+  g.R = rhs_block(nrhs, ctx->rhs_max);
   g.nrb = (nrhs + g.R - 1) / g.R;
   g.npad = g.nrb * g.R;
   return g;

@@ -30,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--ns", type=int, default=-1, help="ring slots of the staged kernel (0: as many as fit)")
     ap.add_argument("--autotune", action="store_true", help="pick the kernel variant with mmc_autotune first")
     ap.add_argument("--graphs", type=int, default=1, help="replay step chains as CUDA graphs")
+    ap.add_argument("--rmax", type=int, default=16, help="largest rhs block of the field layout (8 or 16)")
     ap.add_argument("--deflate", type=int, default=0,
                     help="k > 0: random deflation space of k vectors, levels deflated (tensor-core projections)")
     a = ap.parse_args(argv)
@@ -41,6 +42,7 @@ def main(argv=None):
     prec = mmc.PREC[a.prec]
     ctx = mmc.mmc_create(a.dims, seed=3, device=0)
     try:
+        mmc.mmc_set_rhs_block_max(ctx, a.rmax)
         mmc.mmc_load_gauge(ctx, synth.random_gauge(a.dims, 0.25, 1), 0.1565, 1)
         mmc.mmc_set_step_variant(ctx, prec, a.rpt, a.minb, a.spc)
         mmc.mmc_set_graphs(ctx, a.graphs)
@@ -73,7 +75,7 @@ def main(argv=None):
         p = mmc.mmc_profile_read(ctx)
         vol = int(np.prod(a.dims))
         out = {"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "degree": a.degree,
-               "graphs": a.graphs,
+               "graphs": a.graphs, "rmax": a.rmax,
                "step_launches": p["step_launches"], "avg_launch_ms": p["step_ms"] / max(1, p["step_launches"]),
                "algorithmic_GBps": p["step_bytes"] / p["step_ms"] / 1e6 if p["step_ms"] else 0,
                "TFLOPs": p["step_flops"] / p["step_ms"] / 1e9 if p["step_ms"] else 0,

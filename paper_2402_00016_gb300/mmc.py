@@ -110,6 +110,7 @@ _SIGS = {
     "mmc_set_step_variant_class": (_i, [_vp, _i, _i, _i, _i, _i, _i, _i, _i]),
     "mmc_set_graphs": (_i, [_vp, _i]),
     "mmc_set_solve_storage": (_i, [_vp, _i]),
+    "mmc_set_rhs_block_max": (_i, [_vp, _i]),
     "mmc_graph_note": (ctypes.c_char_p, [_vp]),
     "mmc_set_solve_params": (_i, [_vp, _i, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
@@ -394,6 +395,10 @@ def mmc_profile_read(ctx):
     st = mmc_profile_stats()
     _check(lib.mmc_profile_read(ctx, ctypes.byref(st)), ctx)
     return st.as_dict()
+
+
+def mmc_set_rhs_block_max(ctx, rmax):
+    _check(lib.mmc_set_rhs_block_max(ctx, int(rmax)), ctx)
 
 
 def mmc_set_solve_storage(ctx, prec_inner):

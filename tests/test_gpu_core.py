@@ -286,3 +286,40 @@ def test_chain_graphs_replay_identical(mmc, lat, prec):
             assert np.array_equal(samples[0], samples[k]), k
     finally:
         mmc.mmc_set_graphs(lat.ctx, True)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_rhs_block_max_8(mmc, prec):
+    """A context whose blocked layout holds at most 8 rhs per block gives the same M x
+    (several blocks and a ragged last one) and the same p(M) x as the oracle."""
+    dims = (6, 4, 2, 6)
+    U = synth.random_gauge(dims, 0.5, 11)
+    ctx = mmc.mmc_create(dims, seed=5, device=0)
+    try:
+        mmc.mmc_set_rhs_block_max(ctx, 8)
+        mmc.mmc_load_gauge(ctx, U, 0.13, 1)
+        with pytest.raises(mmc.MMCError):
+            mmc.mmc_set_rhs_block_max(ctx, 4)
+        V = int(np.prod(dims))
+        nrhs = 21
+        assert mmc.mmc_field_bytes(ctx, nrhs, prec) == 24 * V * 12 * (16, 8, 4)[prec]
+        x = mmc.new_field(ctx, nrhs, prec)
+        y = mmc.new_field(ctx, nrhs, prec)
+        mmc.mmc_noise(ctx, 2, 0, mmc.MMC_TAG_NOISE, nrhs, prec, x)
+        mmc.mmc_apply_M(ctx, x, y, nrhs, prec, 0)
+        got = mmc.mmc_unpack(ctx, y, nrhs, prec, V)
+        theta = np.array([1.0 + 0.5j, 1.0 - 0.5j, 0.6 + 0.0j])
+        h = mmc.mmc_poly_from_roots(ctx, theta)
+        mmc.mmc_apply_poly(ctx, h, x, y, nrhs, prec)
+        gotp = mmc.mmc_unpack(ctx, y, nrhs, prec, V)
+        shape = _shape(dims)
+        op = lambda v: wilson.apply_M(U, 0.13, v.reshape(shape), True).ravel()
+        tol = (1e-12, 1e-5, BF16_BOUND)[prec]
+        for j in (0, 7, 8, 20):
+            eta = noise.z4_noise(dims, 5, j, 2).ravel()
+            want = op(eta)
+            assert np.linalg.norm(got[j] - want) / np.linalg.norm(want) < tol, j
+            wantp = krylov.apply_poly(op, theta, eta)
+            assert np.linalg.norm(gotp[j] - wantp) / np.linalg.norm(wantp) < 3 * tol, j
+    finally:
+        mmc.mmc_destroy(ctx)
