@@ -352,6 +352,14 @@ int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner);
  * fields; smaller blocks halve the L2 footprint of a site at the price of more
  * link reads per vector.  MMC_ERR_ARG for other values. */
 int mmc_set_rhs_block_max(mmc_ctx* ctx, int rmax);
+/* Fault injection for tests of the failure path (not part of the method):
+ * enable != 0 makes the producer of the staged step kernel (version 3) issue no
+ * copies, so every wait of its compute warps runs out; each wait is bounded by
+ * wait_iters polls (0: the kernel's default, well over a second).  The kernel
+ * then raises its error flag and returns, and the next synchronising call
+ * (a level, a solve, a reduction) returns MMC_ERR_TIMEOUT with the context
+ * still usable.  enable = 0 restores normal operation. */
+int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters);
 
 /* Launch variant of the fused step kernel for precision prec, for both rhs-block
  * classes (R < 16 and R = 16; mmc_set_step_variant_class sets one): rpt right-hand

@@ -218,6 +218,13 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer) {
   return MMC_OK;
 }
 
+int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters) {
+  if (!ctx || wait_iters < 0) return MMC_ERR_ARG;
+  ctx->stall_test = enable != 0;
+  ctx->wait_iters = wait_iters;
+  return MMC_OK;
+}
+
 int mmc_set_rhs_block_max(mmc_ctx* ctx, int rmax) {
   if (!ctx) return MMC_ERR_ARG;
   if (rmax != 8 && rmax != 16) RET(MMC_ERR_ARG, "mmc_set_rhs_block_max: 8 or 16");

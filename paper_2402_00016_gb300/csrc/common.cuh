@@ -39,6 +39,8 @@ struct step_params {
   int theta;               // 0: 1, 1: gamma_4, 2: gamma_5
   int flags;
   int* err;                // device flag: set by a kernel whose bounded wait gave up (staged form)
+  long long wait_iters;    // bound of each mbarrier wait of the staged form (0: the default)
+  int stall_test;          // fault injection: the staged form's producer issues no copies
 };
 
 template <typename T>

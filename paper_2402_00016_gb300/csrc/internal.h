@@ -90,6 +90,8 @@ struct mmc_ctx {
   std::string graph_note;             // why graphs were switched off, if they were
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
+  long long wait_iters = 0;   // bound of the staged kernel's mbarrier waits (0: its default)
+  int stall_test = 0;         // fault injection for tests: the staged kernel's producer copies nothing
   int rhs_max = 16;           // largest rhs block R of the blocked field layout (8 or 16)
   int solve_inner = MMC_F32;  // inner FGMRES storage of the reduced-precision levels' solves (F32 or BF16)
   std::string err;
@@ -327,6 +329,8 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       p.theta = run.theta;
       p.flags = st.flags | (run.dagger ? mmc::SF_DAGGER : 0);
       p.err = ctx->step_err;
+      p.wait_iters = ctx->wait_iters;
+      p.stall_test = ctx->stall_test;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (events) {
         TRY(prof_event(ctx, &e0));
@@ -374,7 +378,8 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     mix(reinterpret_cast<uintptr_t>(run.rb_len));
     mix(reinterpret_cast<uintptr_t>(run.prec == MMC_F64 ? ctx->links64 : ctx->links32));
     mix(uint64_t(run.theta) | (uint64_t(run.nbx) << 8) | (uint64_t(run.dagger) << 40) | (uint64_t(run.prec) << 48));
-    mix(uint64_t(g.npad) | (uint64_t(g.R) << 32));
+    mix(uint64_t(g.npad) | (uint64_t(g.R) << 32) | (uint64_t(ctx->stall_test) << 63));
+    mix(uint64_t(ctx->wait_iters));
     mix(uint64_t(ctx->var_ver[run.prec][rc]) | (uint64_t(rpt) << 8) | (uint64_t(ctx->var_minb[run.prec][rc]) << 16) |
         (uint64_t(ctx->spc_v[run.prec][rc]) << 24) | (uint64_t(ctx->order_v[run.prec][rc]) << 40) |
         (uint64_t(ctx->var_ns[run.prec][rc]) << 48));

@@ -41,8 +41,8 @@ constexpr int max_threads() { return RPT == 2 ? 224 : 416; }
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
-__device__ __forceinline__ bool bar_wait(uint32_t addr, uint32_t parity) {
-  for (long long i = 0; i < kWait; ++i) {
+__device__ __forceinline__ bool bar_wait(uint32_t addr, uint32_t parity, long long lim) {
+  for (long long i = 0; i < lim; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -55,8 +55,9 @@ __device__ __forceinline__ bool bar_wait(uint32_t addr, uint32_t parity) {
 }
 
 // bounded wait that also gives up when another warp has raised the CTA's abort flag
-__device__ __forceinline__ bool bar_wait_ab(uint32_t addr, uint32_t parity, volatile int* abort_flag) {
-  for (long long i = 0; i < kWait; ++i) {
+__device__ __forceinline__ bool bar_wait_ab(uint32_t addr, uint32_t parity, volatile int* abort_flag,
+                                            long long lim) {
+  for (long long i = 0; i < lim; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -228,6 +229,7 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
   w.n_rows = p.V / Lx;
   w.n_items = w.n_rows * (p.npad / R);
   const size_t rb_elems = size_t(p.V) * 12 * R;
+  const long long lim = p.wait_iters > 0 ? p.wait_iters : kWait;
 
   if (tid == 0) {
     for (int b = 0; b < ns; ++b) {
@@ -250,34 +252,40 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
     long long e = 0;
     int j = 0;
     bool ok = true;
+    // fault injection (tests only): no copy is issued, so the compute warps' waits run out
+    const bool copies = p.stall_test == 0;
     for (int item = w.next(p, blockIdx.x); ok && item < w.n_items; item = w.next(p, item + gridDim.x), ++j) {
       const int rb = item / w.n_rows, row = item % w.n_rows;
       const S* rbase = in + size_t(rb) * rb_elems;
       {  // own row and links into own slot j & 1, released by item j - 2
         const int b = j & 1;
-        if (j >= 2 && !bar_wait_ab(oempty0 + 8 * b, uint32_t(((j >> 1) - 1) & 1), abort_flag)) {
+        if (j >= 2 && !bar_wait_ab(oempty0 + 8 * b, uint32_t(((j >> 1) - 1) & 1), abort_flag, lim)) {
           ok = false;
           break;
         }
         unsigned char* dst = ownb + size_t(b) * slotB;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bar_expect(ofull0 + 8 * b, slotB);
-        bulk_load(su32(dst), rbase + size_t(row) * rowE, rowB, ofull0 + 8 * b);
-        bulk_load(su32(dst + rowB), links + size_t(row) * Lx * 40, linkB, ofull0 + 8 * b);
+        if (copies) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bar_expect(ofull0 + 8 * b, slotB);
+          bulk_load(su32(dst), rbase + size_t(row) * rowE, rowB, ofull0 + 8 * b);
+          bulk_load(su32(dst + rowB), links + size_t(row) * Lx * 40, linkB, ofull0 + 8 * b);
+        }
       }
       for (int k = 0; k < 6; ++k) {  // y+1, y-1, z+1, z-1, t+1, t-1 (backward ones with links)
         const int slot = int(e % ns);
-        if (e >= ns && !bar_wait_ab(empty0 + 8 * slot, uint32_t(((e / ns) - 1) & 1), abort_flag)) {
+        if (e >= ns && !bar_wait_ab(empty0 + 8 * slot, uint32_t(((e / ns) - 1) & 1), abort_flag, lim)) {
           ok = false;
           break;
         }
         const int nr = nbr_row(p, row, k);
         const bool with_links = (k & 1) != 0;
         unsigned char* dst = ringb + size_t(slot) * slotB;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bar_expect(full0 + 8 * slot, rowB + (with_links ? linkB : 0u));
-        bulk_load(su32(dst), rbase + size_t(nr) * rowE, rowB, full0 + 8 * slot);
-        if (with_links) bulk_load(su32(dst + rowB), links + size_t(nr) * Lx * 40, linkB, full0 + 8 * slot);
+        if (copies) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bar_expect(full0 + 8 * slot, rowB + (with_links ? linkB : 0u));
+          bulk_load(su32(dst), rbase + size_t(nr) * rowE, rowB, full0 + 8 * slot);
+          if (with_links) bulk_load(su32(dst + rowB), links + size_t(nr) * Lx * 40, linkB, full0 + 8 * slot);
+        }
         ++e;
       }
     }
@@ -286,8 +294,11 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
       atomicExch(p.err, 1);
     }
     // the last copies issued into each slot land before this thread (and so the CTA) leaves
-    for (long long d = (e > ns ? e - ns : 0); d < e; ++d) bar_wait(full0 + 8 * int(d % ns), uint32_t((d / ns) & 1));
-    for (int d = (j > 2 ? j - 2 : 0); d < j; ++d) bar_wait(ofull0 + 8 * (d & 1), uint32_t((d >> 1) & 1));
+    if (copies) {
+      for (long long d = (e > ns ? e - ns : 0); d < e; ++d)
+        bar_wait(full0 + 8 * int(d % ns), uint32_t((d / ns) & 1), lim);
+      for (int d = (j > 2 ? j - 2 : 0); d < j; ++d) bar_wait(ofull0 + 8 * (d & 1), uint32_t((d >> 1) & 1), lim);
+    }
     return;
   }
 
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
 
     // own row: +-x hops
     {
-      const bool got = bar_wait_ab(ofull0 + 8 * (jo & 1), uint32_t((jo >> 1) & 1), abort_flag);
+      const bool got = bar_wait_ab(ofull0 + 8 * (jo & 1), uint32_t((jo >> 1) & 1), abort_flag, lim);
       if (!(ok = __all_sync(0xffffffffu, got))) break;
     }
     const unsigned char* own = ownb + size_t(jo & 1) * slotB;
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
 #pragma unroll
     for (int k = 1; k < 7; ++k) {
       {
-        const bool got = bar_wait_ab(full0 + 8 * int(e % ns), uint32_t((e / ns) & 1), abort_flag);
+        const bool got = bar_wait_ab(full0 + 8 * int(e % ns), uint32_t((e / ns) & 1), abort_flag, lim);
         if (!(ok = __all_sync(0xffffffffu, got))) break;
       }
       const unsigned char* sb = ringb + size_t(e % ns) * slotB;

@@ -29,6 +29,8 @@ PREC = {"f64": MMC_F64, "f32": MMC_F32, "bf16": MMC_BF16}
 THETA = {"1": MMC_THETA_ONE, "g4": MMC_THETA_G4, "g5": MMC_THETA_G5}
 ERRORS = {-1: "MMC_ERR_ARG", -2: "MMC_ERR_NOMEM", -3: "MMC_ERR_CUDA", -4: "MMC_ERR_BREAKDOWN",
           -5: "MMC_ERR_NOCONV", -6: "MMC_ERR_TIMEOUT", -7: "MMC_ERR_NAN", -8: "MMC_ERR_STATE"}
+(MMC_ERR_ARG, MMC_ERR_NOMEM, MMC_ERR_CUDA, MMC_ERR_BREAKDOWN, MMC_ERR_NOCONV, MMC_ERR_TIMEOUT, MMC_ERR_NAN,
+ MMC_ERR_STATE) = range(-1, -9, -1)
 
 if not os.path.exists(_LIB_PATH):
     raise ImportError("libmmc.so is not built (run __graft_entry__.build() or paper_2402_00016_gb300/build.py)")
@@ -111,6 +113,7 @@ _SIGS = {
     "mmc_set_graphs": (_i, [_vp, _i]),
     "mmc_set_solve_storage": (_i, [_vp, _i]),
     "mmc_set_rhs_block_max": (_i, [_vp, _i]),
+    "mmc_test_stall_staged": (_i, [_vp, _i, ctypes.c_longlong]),
     "mmc_graph_note": (ctypes.c_char_p, [_vp]),
     "mmc_set_solve_params": (_i, [_vp, _i, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
@@ -395,6 +398,11 @@ def mmc_profile_read(ctx):
     st = mmc_profile_stats()
     _check(lib.mmc_profile_read(ctx, ctypes.byref(st)), ctx)
     return st.as_dict()
+
+
+def mmc_test_stall_staged(ctx, enable, wait_iters=0):
+    """Fault injection for tests: the staged step kernel's bounded waits run out."""
+    _check(lib.mmc_test_stall_staged(ctx, int(bool(enable)), int(wait_iters)), ctx)
 
 
 def mmc_set_rhs_block_max(ctx, rmax):
