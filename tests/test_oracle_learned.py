@@ -77,3 +77,21 @@ def test_hop_features_rebuild_wilson_hop():
     ws[1][0] = np.eye(4)
     ws[2][0] = np.eye(4)
     assert np.abs(learned.forward(U, ws, a) - feats[4]).max() < 1e-14
+
+
+def test_adam_closed_form_for_constant_gradient():
+    """Adam's bias corrections make m_hat = g and v_hat = g^2 exactly for a gradient that
+    does not change, so every step moves each real parameter by -lr * g / (|g| + eps);
+    real and imaginary parts are separate parameters."""
+    rng = np.random.default_rng(3)
+    W = [rng.standard_normal((2, 3)) + 1j * rng.standard_normal((2, 3))]
+    G = [rng.standard_normal((2, 3)) + 1j * rng.standard_normal((2, 3))]
+    G[0][0, 0] = 0.5 - 2.0j
+    lr, eps = 0.01, 1e-8
+    state = {}
+    cur = W
+    for t in range(1, 6):
+        cur = learned.adam_step(cur, G, state, lr, eps=eps)
+        step = lr * (G[0].real / (np.abs(G[0].real) + eps) + 1j * G[0].imag / (np.abs(G[0].imag) + eps))
+        assert np.allclose(cur[0], W[0] - t * step, rtol=0, atol=1e-12)
+    assert state["t"] == 5
