@@ -25,7 +25,8 @@
  *     complex128; of the gauge field: [mu][t][z][y][x][row][col] complex128,
  *     mu = 0:x, 1:y, 2:z, 3:t.
  *   - Device field layout ("blocked"): [rb][site][c][R] complex, c = 3*spin +
- *     colour, R = mmc_rhs_block(nrhs) right-hand sides per block, rb = 0 ..
+ *     colour, R = mmc_rhs_block(nrhs) right-hand sides per block (at most 8
+ *     on a context set by mmc_set_rhs_block_max(ctx, 8)), rb = 0 ..
  *     ceil(nrhs/R)-1; padding RHS slots are kept at zero.  Storage type per
  *     precision: MMC_F64 complex double (16 B), MMC_F32 complex float (8 B),
  *     MMC_BF16 two bfloat16 (4 B).  mmc_field_bytes() gives the size.
@@ -107,7 +108,8 @@ const char* mmc_last_error(const mmc_ctx* ctx);
 /* Noise seed of the context; may be changed between calls. */
 int mmc_set_seed(mmc_ctx* ctx, uint64_t seed);
 
-/* RHS block R used for a batch of nrhs vectors (power of two, <= 16). */
+/* RHS block R used for a batch of nrhs vectors (power of two, <= 16) on a
+ * context with the default layout (see mmc_set_rhs_block_max). */
 int mmc_rhs_block(int nrhs);
 /* Bytes of a device field of nrhs vectors in precision prec (blocked layout). */
 size_t mmc_field_bytes(const mmc_ctx* ctx, int nrhs, int prec);
