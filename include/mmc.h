@@ -338,17 +338,19 @@ int mmc_profile(mmc_ctx* ctx, int enable);
 int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out);
 
 /* Inner FGMRES length and outer-cycle limit of the solves inside mmc_trace_level
- * (defaults 48 and 400).  Values <= 0 keep the current setting. */
+ * (Sec. 1 and Sec. 8: the solves of the M^-1 level; defaults 48 and 400).
+ * Values <= 0 keep the current setting. */
 int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
 /* Storage of the inner FGMRES stage (its preconditioner chain included) in the
- * solves of the M^-1 level of a reduced-precision mmc_trace_level (the
- * prec_inner of mmc_solve): MMC_F32 (default) or MMC_BF16.  The FP64 outer loop
- * still refines every solve to a relative residual of 1e-10, so the level's
- * samples differ only within that tolerance; a flexible inner iteration absorbs
- * the BF16 rounding of the preconditioner.  MMC_ERR_ARG for any other value. */
+ * solves of the M^-1 level of a reduced-precision mmc_trace_level (Sec. 1,
+ * Sec. 8; the prec_inner of mmc_solve): MMC_F32 (default) or MMC_BF16.  The FP64
+ * outer loop still refines every solve to a relative residual of 1e-10, so the
+ * level's samples differ only within that tolerance; the flexible inner
+ * iteration tolerates the less accurate preconditioner at the cost of more
+ * iterations.  MMC_ERR_ARG for any other value. */
 int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner);
-/* Largest right-hand-side block R of the blocked field layout [rb][site][c][R]
- * (8 or 16, default 16).  A batch of N vectors uses R = min(rmax, next power of
+/* Not part of the paper (data layout): largest right-hand-side block R of the
+ * blocked field layout [rb][site][c][R] (8 or 16, default 16).  A batch of N vectors uses R = min(rmax, next power of
  * two >= N).  It changes the layout of every field sized or interpreted after
  * the call (mmc_field_bytes, mmc_pack, mmc_unpack), so set it before creating
  * fields; smaller blocks halve the L2 footprint of a site at the price of more
@@ -363,7 +365,8 @@ int mmc_set_rhs_block_max(mmc_ctx* ctx, int rmax);
  * still usable.  enable = 0 restores normal operation. */
 int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters);
 
-/* Launch variant of the fused step kernel for precision prec, for both rhs-block
+/* Not part of the paper (launch tuning of the a1/a5 step kernel, Sec. 1 and
+ * Sec. 3).  Launch variant of the fused step kernel for precision prec, for both rhs-block
  * classes (R < 16 and R = 16; mmc_set_step_variant_class sets one): rpt right-hand
  * sides per lane (1, 2; F64 uses 1), minb = minimum resident CTAs per SM asked
  * of the compiler for the generic kernel (1: no register cap; 3 or 4: capped),
@@ -386,16 +389,18 @@ int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int versio
                                int blocked, int ns);
 /* Step chains (the degrees of a polynomial applied to a batch, Sec. 3, Sec. 5) run
  * as CUDA graphs: the first run of a chain with given operands, coefficients and
- * kernel variant captures its launches, later runs replay the graph (one launch
- * for all degrees).  enable = 0 launches every degree directly (and drops the
- * graphs); results are identical either way.  Default: enabled.  A chain called
- * while the caller's stream is already capturing is launched directly into the
- * caller's capture. */
+ * kernel variant captures its launches (on a private stream of the context),
+ * later runs replay the graph on the caller's stream (one launch for all
+ * degrees).  enable = 0 launches every degree directly (and drops the graphs);
+ * results are identical either way.  Default: enabled.  While the caller's
+ * stream is itself capturing, chains are launched degree by degree.  Returns
+ * MMC_ERR_ARG for a NULL context. */
 int mmc_set_graphs(mmc_ctx* ctx, int enable);
 /* "" while chain graphs work; otherwise why the context switched to direct
  * launches (a capture the driver refused).  Context-owned string. */
 const char* mmc_graph_note(const mmc_ctx* ctx);
-/* Autotuner: time every step-kernel variant on an nrhs-vector field of
+/* Not part of the paper (launch tuning).  Autotuner: time every step-kernel
+ * variant (M alone, without an epilogue) on an nrhs-vector field of
  * precision prec (random data, CUDA events, median of 3 after a warm-up),
  * keep the fastest for that precision and the rhs-block class of nrhs and
  * return it (best[6] = rpt, minb, spc, kernel version, blocked traversal, ring
