@@ -187,10 +187,12 @@ int mmc_apply_poly(mmc_ctx* ctx, int handle, const void* x, void* y, int nrhs, i
  * (lambda = z^H M z, accepted if ||M z - lambda z|| < tol_accept, Sec. 8: 1e-3);
  * the accepted ones of smallest |lambda|, at most k, are kept with left vectors
  * u_i = gamma5 z_j (lambda_j = conj lambda_i; |Im| < 2e-4 counts as real;
- * equal eigenvalues take distinct partners) and U^H Z = I.  If the overlap
- * W^H Z of the kept vectors is singular or its inverse exceeds 1e6, the pairs of
- * largest |lambda| are dropped until it is not (MMC_ERR_BREAKDOWN if none is
- * left).  lambda_out (2k doubles, may be NULL) receives the eigenvalues. */
+ * equal eigenvalues take distinct partners) and U^H Z = I.  While the overlap
+ * W^H Z of the kept vectors is singular the pair of largest |lambda| is dropped,
+ * and while a column of its inverse (the size of a left vector u_i, which the
+ * deflated samples carry) has norm above 100 the pair with the largest one is
+ * dropped together with its gamma5 partner (MMC_ERR_BREAKDOWN if none is left).  lambda_out (2k doubles, may be
+ * NULL) receives the eigenvalues of the kept pairs. */
 int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arnoldi, double tol_accept,
                 double* lambda_out, int* k_accepted);
 

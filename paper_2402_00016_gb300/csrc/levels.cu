@@ -449,20 +449,57 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
       TRY(reduce_to_host(ctx, (double2*)part, nbx, kk, 1, col, s));
       for (int i = 0; i < kk; ++i) S(i, j) = col[i];
     }
-    // a singular or ill-conditioned overlap drops the pairs of largest |lambda| until it is not
+    // Variance control: with unit w_j, ||u_i|| follows the norm of column i of
+    // Inv = (W^H Z)^{-H}, which grows where the kept set is nearly dependent, and the
+    // deflated sample carries (eta^H Theta z_i)(u_i^H eta).  While the overlap is
+    // singular, drop the pair of largest |lambda|; while a column norm exceeds kMaxU,
+    // drop the pair with the largest one (with its partner).
+    const double kMaxU = 100.0;
+    std::vector<int> sel(kk);
+    for (int i = 0; i < kk; ++i) sel[i] = i;
     CMat Inv;
-    for (; kk > 0; --kk) {
-      CMat SH(kk, kk);
-      Inv = CMat(kk, kk);
-      for (int i = 0; i < kk; ++i)
-        for (int j = 0; j < kk; ++j) SH(i, j) = std::conj(S(j, i));
-      for (int i = 0; i < kk; ++i) Inv(i, i) = 1.0;
-      if (!mmc::lu_solve(SH, Inv)) continue;
-      double big = 0;  // |u_i| grows with 1/|S|
-      for (const cd& v : Inv.a) big = std::max(big, std::abs(v));
-      if (big < 1e6) break;
+    while (!sel.empty()) {
+      const int q = int(sel.size());
+      CMat SH(q, q);
+      Inv = CMat(q, q);
+      for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) SH(i, j) = std::conj(S(sel[j], sel[i]));
+      for (int i = 0; i < q; ++i) Inv(i, i) = 1.0;
+      if (!mmc::lu_solve(SH, Inv)) {
+        sel.pop_back();
+        continue;
+      }
+      int imax = 0;
+      double cmax = -1;
+      for (int i = 0; i < q; ++i) {
+        double c2 = 0;
+        for (int j = 0; j < q; ++j) c2 += std::norm(Inv(j, i));
+        if (c2 > cmax) {
+          cmax = c2;
+          imax = i;
+        }
+      }
+      if (std::isfinite(cmax) && std::sqrt(cmax) <= kMaxU) break;
+      // drop the pair together with its gamma_5 partner, so the kept eigenvalues stay
+      // in partner pairs (conjugates, or real)
+      const int victim = sel[imax];
+      int mate = -1;
+      for (int i = 0; i < q; ++i)
+        if (i != imax && keep[sel[i]] == partner[victim]) mate = i;
+      if (mate > imax) sel.erase(sel.begin() + mate);
+      sel.erase(sel.begin() + imax);
+      if (mate >= 0 && mate < imax) sel.erase(sel.begin() + mate);
     }
+    kk = int(sel.size());
     if (kk == 0) RET(MMC_ERR_BREAKDOWN, "mmc_deflate: W^H Z is singular");
+    // compact Z and W to the selection (sel increases, so every copy moves a vector forward)
+    for (int p2 = 0; p2 < kk; ++p2) {
+      if (sel[p2] == p2) continue;
+      CK(cudaMemcpyAsync(reinterpret_cast<char*>(ctx->Z) + size_t(p2) * fb,
+                         reinterpret_cast<char*>(ctx->Z) + size_t(sel[p2]) * fb, fb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(reinterpret_cast<char*>(W) + size_t(p2) * fb, reinterpret_cast<char*>(W) + size_t(sel[p2]) * fb,
+                         fb, cudaMemcpyDeviceToDevice, s));
+    }
     // Inv = S^{-H};  U_i = sum_j W_j Inv(j, i)
     for (int i = 0; i < kk; ++i) {
       std::vector<cd> h(kk);
@@ -479,7 +516,7 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
     CK(mmc::launch_convert(MMC_F32, ctx->Z32, MMC_F64, ctx->Z, gk, s));
     CK(mmc::launch_convert(MMC_F32, ctx->U32, MMC_F64, ctx->U, gk, s));
     CK(cudaStreamSynchronize(s));
-    for (int i = 0; i < kk; ++i) ctx->lambda.push_back(lam[keep[i]]);
+    for (int i = 0; i < kk; ++i) ctx->lambda.push_back(lam[keep[sel[i]]]);
     ctx->k_defl = kk;
   }
   *k_accepted = kk;
