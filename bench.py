@@ -105,6 +105,7 @@ def level_plan(h):
 # matvecs per sample of the polynomial parts (solves excluded) -- used to scale the CPU legs
 POLY_MATVECS = 8 * 319 + 32 * (319 + 128) + 128 * (128 + 32) + 512 * (32 + 8)
 SAMPLES = 8 + 32 + 128 + 512
+LEVELS = ["M^-1 - p_dbl(40x8)", "p_dbl - p_128", "p_128 - p_32", "p_32 - p_8"]
 # DRAM traffic / algorithmic bytes of the level-chain step kernel, measured by ncu on 24^4 with
 # 64 right-hand sides (6.704 GB of dram__bytes_read+write against 4.544 GB algorithmic)
 TRAFFIC_RATIO = 6.704 / 4.544
@@ -142,7 +143,9 @@ def run_reference(args, rank):
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "lattice": "24^4", "kappa": W.kappa, "eps": W.eps},
+            "config": {"workload": WORKLOAD, "lattice": "24^4", "eps": W.eps, "kappa": W.kappa,
+                       "levels": LEVELS, "noises": [8, 32, 128, 512], "storage": "f64 (oracle)",
+                       "parallelism": "1 host core"},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "samples/s", "cores": 1,
                              "sample": "per step: one degree-2 polynomial sample (2 oracle matvecs) at 24^4; "
                                        "samples/s scaled by the workload's %.1f polynomial matvecs per sample "
@@ -341,7 +344,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": "24^4", "eps": W.eps, "kappa": W.kappa,
-                   "levels": ["M^-1 - p_dbl(40x8)", "p_dbl - p_128", "p_128 - p_32", "p_32 - p_8"],
+                   "levels": LEVELS,
                    "noises": [8, 32, 128, 512], "storage": args.storage, "arithmetic": "fp32, fp64 bilinears",
                    "deflated": len(lam), "probe_colours": ncol,
                    "solves": {"fgmres_m": args.solve_m, "precond": "p_in (degree 39)" if args.precond == "in"
