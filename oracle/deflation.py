@@ -10,68 +10,134 @@ is below ``tol_accept`` (1e-3 in Sec. 8); values with |Im lambda| below
 The paper says only that the left eigenvectors "are found".  Reading taken:
 gamma_5-hermiticity (gamma5 M gamma5 = M^+) makes gamma5 z a left eigenvector
 for conj(lambda); so u_i = gamma5 z_j with lambda_j the conjugate partner of
-lambda_i (j = i for real lambda_i).  Eigenvalues whose partner is not among
-the accepted ones are dropped.  Finally U is rescaled so that U^H Z = I
-(biorthonormal), U = W (W^H Z)^{-H}.
+lambda_i (j = i for real lambda_i); equal eigenvalues take distinct partners.
+Eigenvalues whose partner is not among the kept ones are dropped.  U is
+rescaled so that U^H Z = I (biorthonormal), U = W (W^H Z)^{-H}.  Two further
+rules bound the variance that the deflated samples carry through
+(eta^H Theta z_i)(u_i^H eta): while W^H Z is singular the pair of largest
+|lambda| is dropped, and while a column of (W^H Z)^{-H} (whose norm is the
+norm of u_i for unit w) exceeds ``max_u`` = 100 in norm the pair with the
+largest one is dropped; a dropped pair takes its gamma_5 partner with it, so
+the kept eigenvalues stay closed under conjugation.  Any kept set keeps the
+estimator unbiased (Eq. 2 with an exactly traced deflated part, Sec. 7).
 """
 import numpy as np
 
 from . import krylov
 
 
+def select_pairs(lam, res, k, tol_accept=1e-3, real_tol=2e-4):
+    """Kept candidates and their gamma_5 partners (Sec. 8 acceptance, reading above).
+
+    ``lam``, ``res``: Rayleigh quotients and residual norms of the candidate
+    Ritz vectors.  Accepted: res < tol_accept (finite).  The accepted ones are
+    ordered by |lambda| (stable) and the first k considered.  In that order a
+    real lambda (|Im| < real_tol) is its own partner; a complex one takes the
+    nearest considered candidate to conj(lambda), other than itself and not
+    already taken as a partner, if it lies within 10 max(real_tol, 1e-6
+    |lambda|); otherwise it is dropped.  Returns (keep, partner): lists of
+    candidate indices, partner[i] belonging to keep[i].
+    """
+    lam = np.asarray(lam, dtype=np.complex128)
+    res = np.asarray(res, dtype=np.float64)
+    acc = [i for i in range(lam.size) if np.isfinite(res[i]) and res[i] < tol_accept]
+    acc = sorted(acc, key=lambda i: abs(lam[i]))[:k]  # sorted() is stable
+    taken = set()
+    keep, partner = [], []
+    for a in acc:
+        l = lam[a]
+        if abs(l.imag) < real_tol:
+            keep.append(a)
+            partner.append(a)
+            continue
+        best, bd = None, np.inf
+        for b in acc:
+            if b == a or b in taken:
+                continue
+            d = abs(lam[b] - np.conj(l))
+            if d < bd:
+                best, bd = b, d
+        if best is not None and bd < 10 * max(real_tol, 1e-6 * abs(l)):
+            keep.append(a)
+            partner.append(best)
+            taken.add(best)
+    return keep, partner
+
+
+def condition_selection(S, mates, max_u=100.0):
+    """Drop rules on the overlap S = W^H Z of the kept pairs (reading above).
+
+    ``S``: q x q complex, S[i, j] = w_i^H z_j; ``mates[i]``: position of pair
+    i's gamma_5 partner among the q (i itself for a real eigenvalue).  Starting
+    from all positions in order: if S restricted to the selection is singular,
+    drop the last selected position (the largest |lambda|) and its partner;
+    else form Inv = (S_sel)^{-H}; if the largest column norm of Inv exceeds
+    max_u, drop that column's position and its partner; else stop.
+    Returns (sel, Inv): the kept positions (increasing) and the inverse.
+    """
+    S = np.asarray(S, dtype=np.complex128)
+    sel = list(range(S.shape[0]))
+    while sel:
+        Ssel = S[np.ix_(sel, sel)]
+        try:
+            Inv = np.linalg.inv(Ssel.conj().T)
+        except np.linalg.LinAlgError:
+            victim = len(sel) - 1
+        else:
+            norms = np.sqrt(np.sum(np.abs(Inv) ** 2, axis=0))
+            victim = int(np.argmax(norms))  # first maximum
+            if np.isfinite(norms[victim]) and norms[victim] <= max_u:
+                return sel, Inv
+        v = sel[victim]
+        drop = {v, mates[v]}
+        sel = [s for s in sel if s not in drop]
+    return [], np.zeros((0, 0), dtype=np.complex128)
+
+
 def pp_arnoldi_eigenpairs(op, gamma5, theta_poly, b, m_arnoldi, k, tol_accept=1e-3, real_tol=2e-4,
-                          n_candidates=None):
+                          max_u=100.0):
     """Return (lambda, Z, U, residuals) for up to k smallest eigenpairs, U^H Z = I.
 
     ``op`` applies M to a flat vector, ``gamma5`` applies gamma_5 to a flat vector,
-    ``theta_poly`` are the Leja-ordered roots of the preconditioning polynomial p.
-    Reading taken for "the smallest Ritz vectors" (Sec. 8): the Ritz vectors of
-    the ``n_candidates`` (default: all m) Ritz values of phi(M) smallest in
-    modulus are each tested against M (Rayleigh quotient, residual); the
-    accepted ones are ordered by |lambda| and the first k kept.  When the
-    spectrum of M surrounds the origin, phi(lambda) for the smallest lambda
-    need not be the smallest |phi|, so selecting on phi alone would miss them.
+    ``theta_poly`` are the Leja-ordered roots of the preconditioning polynomial p
+    (an empty list: phi = M itself).  Reading taken for "the smallest Ritz
+    vectors" (Sec. 8): every Ritz vector of phi(M) is tested against M (Rayleigh
+    quotient, residual), and the accepted ones of smallest |lambda| are kept
+    (select_pairs, condition_selection).  When the spectrum of M surrounds the
+    origin, phi(lambda) for the smallest lambda need not be the smallest |phi|,
+    so selecting on phi alone would miss them.
     """
-    phi = lambda v: op(krylov.apply_poly(op, theta_poly, v))
+    if len(theta_poly):
+        phi = lambda v: op(krylov.apply_poly(op, theta_poly, v))
+    else:
+        phi = op
     V, H, _ = krylov.arnoldi(phi, b, m_arnoldi)
     mu, G = np.linalg.eig(H[:m_arnoldi, :m_arnoldi])
-    ncand = min(m_arnoldi, n_candidates if n_candidates is not None else m_arnoldi)
-    order = np.argsort(np.abs(mu), kind="stable")[:ncand]
-    lam, Zs, res = [], [], []
-    for i in order:
+    lam = np.zeros(m_arnoldi, dtype=np.complex128)
+    res = np.zeros(m_arnoldi)
+    Zc = []
+    for i in range(m_arnoldi):
         z = V[:, :m_arnoldi] @ G[:, i]
         z = z / np.linalg.norm(z)
         Mz = op(z)
-        l = np.vdot(z, Mz)
-        r = np.linalg.norm(Mz - l * z)
-        if r < tol_accept:
-            lam.append(l)
-            Zs.append(z)
-            res.append(r)
-    by_size = np.argsort(np.abs(np.array(lam)), kind="stable")[:k]
-    lam = np.array(lam, dtype=np.complex128)[by_size]
-    Zs = [Zs[i] for i in by_size]
-    res = [res[i] for i in by_size]
-    keep, partner = [], []
-    for i, l in enumerate(lam):
-        if abs(l.imag) < real_tol:
-            keep.append(i)
-            partner.append(i)
-            continue
-        d = np.abs(lam - np.conj(l))
-        d[i] = np.inf
-        j = int(np.argmin(d))
-        if d[j] < max(real_tol, 1e-6 * abs(l)) * 10:
-            keep.append(i)
-            partner.append(j)
+        lam[i] = np.vdot(z, Mz)
+        res[i] = np.linalg.norm(Mz - lam[i] * z)
+        Zc.append(z)
+    keep, partner = select_pairs(lam, res, k, tol_accept, real_tol)
+    n = b.size
     if not keep:
-        n = b.size
-        return (np.zeros(0, complex), np.zeros((n, 0), complex), np.zeros((n, 0), complex),
-                np.zeros(0))
-    Z = np.stack([Zs[i] for i in keep], axis=1)
-    W = np.stack([gamma5(Zs[j]) for j in partner], axis=1)
-    U = biorthonormalise(Z, W)
-    return lam[keep], Z, U, np.array(res)[keep]
+        return (np.zeros(0, complex), np.zeros((n, 0), complex), np.zeros((n, 0), complex), np.zeros(0))
+    Z = np.stack([Zc[i] for i in keep], axis=1)
+    W = np.stack([gamma5(Zc[j]) for j in partner], axis=1)
+    pos = {c: i for i, c in enumerate(keep)}
+    mates = [pos.get(partner[i], i) for i in range(len(keep))]
+    sel, Inv = condition_selection(W.conj().T @ Z, mates, max_u)
+    if not sel:
+        return (np.zeros(0, complex), np.zeros((n, 0), complex), np.zeros((n, 0), complex), np.zeros(0))
+    Z = Z[:, sel]
+    U = W[:, sel] @ Inv
+    kept = [keep[i] for i in sel]
+    return lam[kept], Z, U, res[kept]
 
 
 def biorthonormalise(Z, W):

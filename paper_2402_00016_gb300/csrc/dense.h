@@ -40,6 +40,22 @@ bool harmonic_ritz(const CMat& H, int m, std::vector<cd>& theta);
 // sum of log distances to the chosen points; ties to the lowest index.
 std::vector<cd> leja_order(const std::vector<cd>& pts);
 
+// Kept candidates of the deflation (Sec. 8 acceptance): those with res < tol_accept,
+// ordered by |lambda| (stable), the first k; a real one (|Im| < real_tol) is its own
+// gamma_5 partner, a complex one takes the nearest candidate to its conjugate that is
+// neither itself nor already taken, within 10 max(real_tol, 1e-6 |lambda|), else it is
+// dropped.  keep[i], partner[i]: candidate indices.
+void deflation_pairs(const std::vector<cd>& lam, const std::vector<double>& res, double tol_accept, int k,
+                     double real_tol, std::vector<int>& keep, std::vector<int>& partner);
+
+// Drop rules on the q x q overlap S(i, j) = w_i^H z_j of the kept pairs: while S
+// restricted to the selection is singular drop the last position, while a column of
+// its inverse conjugate transpose has norm above max_u drop the position of the
+// largest; each drop takes the position's partner mates[pos] with it.  sel: kept
+// positions (increasing); Inv = (S_sel)^{-H}.  Returns false if nothing is left.
+bool deflation_condition(const CMat& S, const std::vector<int>& mates, double max_u, std::vector<int>& sel,
+                         CMat& Inv);
+
 // Scalar p(a) of the Leja recurrence (Sec. 3) and pi(a) = prod (1 - a/theta).
 cd poly_scalar(const std::vector<cd>& theta, cd a);
 cd pi_scalar(const std::vector<cd>& theta, cd a);

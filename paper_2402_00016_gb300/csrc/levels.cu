@@ -380,41 +380,10 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
     TRY(norms2(ctx, MMC_F64, g, Rv, rn, s));
     res[i] = std::sqrt(rn[0]);
   }
-  std::vector<int> acc;
-  for (int i = 0; i < m_arn; ++i)
-    if (res[i] < tol_accept && std::isfinite(res[i])) acc.push_back(i);
-  std::stable_sort(acc.begin(), acc.end(), [&](int a, int b) { return std::abs(lam[a]) < std::abs(lam[b]); });
-  if (int(acc.size()) > k) acc.resize(k);
-  // left vectors from gamma5-hermiticity: partner with conj(lambda), |Im| < 2e-4 counts as real
-  const double real_tol = 2e-4;
-  // A degenerate eigenvalue gives several accepted vectors with (nearly) equal lambda:
-  // each takes a different partner (the nearest one not yet taken), so the left
-  // vectors stay independent.
+  // kept candidates and their gamma_5 partners (Sec. 8 acceptance; left vectors from
+  // gamma_5-hermiticity, |Im| < 2e-4 counts as real)
   std::vector<int> keep, partner;
-  std::vector<char> taken(m_arn, 0);
-  for (size_t a = 0; a < acc.size(); ++a) {
-    cd l = lam[acc[a]];
-    if (std::abs(l.imag()) < real_tol) {
-      keep.push_back(acc[a]);
-      partner.push_back(acc[a]);
-      continue;
-    }
-    int best = -1;
-    double bd = 1e300;
-    for (size_t b2 = 0; b2 < acc.size(); ++b2) {
-      if (b2 == a || taken[acc[b2]]) continue;
-      double d = std::abs(lam[acc[b2]] - std::conj(l));
-      if (d < bd) {
-        bd = d;
-        best = acc[b2];
-      }
-    }
-    if (best >= 0 && bd < std::max(real_tol, 1e-6 * std::abs(l)) * 10) {
-      keep.push_back(acc[a]);
-      partner.push_back(best);
-      taken[best] = 1;
-    }
-  }
+  mmc::deflation_pairs(lam, res, tol_accept, k, 2e-4, keep, partner);
   int kk = int(keep.size());
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
@@ -452,44 +421,18 @@ int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arn, double tol_acce
     // Variance control: with unit w_j, ||u_i|| follows the norm of column i of
     // Inv = (W^H Z)^{-H}, which grows where the kept set is nearly dependent, and the
     // deflated sample carries (eta^H Theta z_i)(u_i^H eta).  While the overlap is
-    // singular, drop the pair of largest |lambda|; while a column norm exceeds kMaxU,
-    // drop the pair with the largest one (with its partner).
-    const double kMaxU = 100.0;
-    std::vector<int> sel(kk);
-    for (int i = 0; i < kk; ++i) sel[i] = i;
-    CMat Inv;
-    while (!sel.empty()) {
-      const int q = int(sel.size());
-      CMat SH(q, q);
-      Inv = CMat(q, q);
-      for (int i = 0; i < q; ++i)
-        for (int j = 0; j < q; ++j) SH(i, j) = std::conj(S(sel[j], sel[i]));
-      for (int i = 0; i < q; ++i) Inv(i, i) = 1.0;
-      if (!mmc::lu_solve(SH, Inv)) {
-        sel.pop_back();
-        continue;
-      }
-      int imax = 0;
-      double cmax = -1;
-      for (int i = 0; i < q; ++i) {
-        double c2 = 0;
-        for (int j = 0; j < q; ++j) c2 += std::norm(Inv(j, i));
-        if (c2 > cmax) {
-          cmax = c2;
-          imax = i;
-        }
-      }
-      if (std::isfinite(cmax) && std::sqrt(cmax) <= kMaxU) break;
-      // drop the pair together with its gamma_5 partner, so the kept eigenvalues stay
-      // in partner pairs (conjugates, or real)
-      const int victim = sel[imax];
-      int mate = -1;
-      for (int i = 0; i < q; ++i)
-        if (i != imax && keep[sel[i]] == partner[victim]) mate = i;
-      if (mate > imax) sel.erase(sel.begin() + mate);
-      sel.erase(sel.begin() + imax);
-      if (mate >= 0 && mate < imax) sel.erase(sel.begin() + mate);
+    // singular the pair of largest |lambda| is dropped, while a column norm exceeds
+    // the bound (100 by default) the pair with the largest one; either drop takes the
+    // gamma_5 partner along.
+    std::vector<int> mates(kk);
+    for (int i = 0; i < kk; ++i) {
+      mates[i] = i;
+      for (int j = 0; j < kk; ++j)
+        if (j != i && keep[j] == partner[i]) mates[i] = j;
     }
+    std::vector<int> sel;
+    CMat Inv;
+    mmc::deflation_condition(S, mates, ctx->defl_max_u, sel, Inv);
     kk = int(sel.size());
     if (kk == 0) RET(MMC_ERR_BREAKDOWN, "mmc_deflate: W^H Z is singular");
     // compact Z and W to the selection (sel increases, so every copy moves a vector forward)
@@ -849,6 +792,26 @@ int mmc_probe_colours(mmc_ctx* ctx, int reach, int* n_colours) {
   if (!ctx || reach < 0 || !n_colours) return MMC_ERR_ARG;
   Colouring c = find_colouring(ctx->dims, ctx->V, reach);
   *n_colours = c.n;
+  return MMC_OK;
+}
+
+int mmc_probe_colouring(const int dims[4], int reach, int* colour, int* n_colours) {
+  if (!dims || reach < 0 || !n_colours) return MMC_ERR_ARG;
+  long long V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 2) return MMC_ERR_ARG;
+    V *= dims[m];
+  }
+  if (V > (1ll << 30)) return MMC_ERR_ARG;
+  Colouring c = find_colouring(dims, int(V), reach);
+  *n_colours = c.n;
+  if (colour) std::copy(c.colour.begin(), c.colour.end(), colour);
+  return MMC_OK;
+}
+
+int mmc_set_deflation_bound(mmc_ctx* ctx, double max_u) {
+  if (!ctx || !(max_u > 0)) return MMC_ERR_ARG;
+  ctx->defl_max_u = max_u;
   return MMC_OK;
 }
 
