@@ -187,14 +187,22 @@ int mmc_apply_poly(mmc_ctx* ctx, int handle, const void* x, void* y, int nrhs, i
  * (lambda = z^H M z, accepted if ||M z - lambda z|| < tol_accept, Sec. 8: 1e-3);
  * the accepted ones of smallest |lambda|, at most k, are kept with left vectors
  * u_i = gamma5 z_j (lambda_j = conj lambda_i; |Im| < 2e-4 counts as real;
- * equal eigenvalues take distinct partners) and U^H Z = I.  While the overlap
- * W^H Z of the kept vectors is singular the pair of largest |lambda| is dropped,
- * and while a column of its inverse (the size of a left vector u_i, which the
- * deflated samples carry) has norm above 100 the pair with the largest one is
- * dropped together with its gamma5 partner (MMC_ERR_BREAKDOWN if none is left).  lambda_out (2k doubles, may be
+ * equal eigenvalues take distinct partners; mmc_deflation_pairs) and U^H Z = I.
+ * While the overlap W^H Z of the kept vectors is singular the pair of largest
+ * |lambda| is dropped, and while a column of its inverse (the size of a left
+ * vector u_i, which the deflated samples carry) has norm above the bound of
+ * mmc_set_deflation_bound (100) the pair with the largest one is dropped; each
+ * drop takes the gamma5 partner along (mmc_deflation_condition;
+ * MMC_ERR_BREAKDOWN if none is left).  lambda_out (2k doubles, may be
  * NULL) receives the eigenvalues of the kept pairs. */
 int mmc_deflate(mmc_ctx* ctx, int k, int poly_handle, int m_arnoldi, double tol_accept,
                 double* lambda_out, int* k_accepted);
+
+/* Bound of mmc_deflate's column-norm rule: pairs are dropped while a left vector
+ * u_i (a column of (W^H Z)^{-H}, unit w) has norm above max_u (default 100; a
+ * reading, not the paper's: it bounds the variance the deflated samples carry).
+ * MMC_ERR_ARG unless max_u > 0. */
+int mmc_set_deflation_bound(mmc_ctx* ctx, double max_u);
 
 /* Replace the deflation data by k caller-given eigenpairs (Sec. 7): lambda (2k
  * doubles), right vectors Z and left vectors U (k vectors each, canonical host
@@ -281,6 +289,11 @@ int mmc_trace_exact(mmc_ctx* ctx, int handle, int theta_op, int method, int prec
 
 /* Number of colours of the probing colouring chosen for a reach (L1 distance). */
 int mmc_probe_colours(mmc_ctx* ctx, int reach, int* n_colours);
+/* The probing colouring itself (Sec. 6), pure host: for a lattice dims[4] =
+ * {Lx, Ly, Lz, Lt} and a reach (periodic L1 distance), colour[V] (may be NULL;
+ * site order x fastest) receives each site's colour and *n_colours their number.
+ * Two distinct sites of equal colour are farther apart than reach. */
+int mmc_probe_colouring(const int dims[4], int reach, int* colour, int* n_colours);
 
 /* ------------------------------------------------- learned network (no paper section) */
 
@@ -320,7 +333,9 @@ int mmc_net_train(mmc_ctx* ctx, int handle, const void* eta, const void* xs, int
 /* Counters of the fused step kernel (the stencil / polynomial-step hot loop):
  * launches, summed CUDA-event time of those launches, algorithmic bytes (each
  * input, output, aux and accumulator element once, the 4 links of a site once
- * per rhs block, the noise codes once) and flops (1368 per site and active
+ * per launch, 72 B each in FP32 and 144 B in FP64; the Z(4) noise of a code
+ * bilinear is not counted, since it could be regenerated from the counter-based
+ * generator instead of read) and flops (1368 per site and active
  * rhs for a hop, 48 more per epilogue term), plus the number of every kernel
  * the library launched.  Not part of the paper: bookkeeping for measurement. */
 typedef struct {
@@ -371,22 +386,29 @@ int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters);
  * Sec. 3).  Launch variant of the fused step kernel for precision prec, for both rhs-block
  * classes (R < 16 and R = 16; mmc_set_step_variant_class sets one): rpt right-hand
  * sides per lane (1, 2; F64 uses 1), minb = minimum resident CTAs per SM asked
- * of the compiler for the generic kernel (1: no register cap; 3 or 4: capped),
- * or 100 + v to select kernel version v (1: generic; 2: rhs block and epilogue
- * fixed at compile time, for F32/BF16 batches with R = 8 or 16; 3: as 2, with
- * the lattice rows staged in shared memory by bulk asynchronous copies issued
- * by a producer warp, for Lx * R up to 384, falling back to 2 otherwise), or
- * 200 + b to traverse the sites in 4 x 4 x 2 x 2 blocks (b = 1, version 2,
- * extents divisible) or lexicographically (b = 0), or 300 + n to give version 3
- * n ring slots (2..6; 300: as many as fit); spc = sites per CTA (16..1024,
- * power of two).  Values <= 0 keep the current setting.  Version 3 bounds every
+ * of the compiler for the generic kernel (1: no register cap; 3 or 4: capped;
+ * for version 4, 3 gives 168 registers and 4 gives 128), or 100 + v to select
+ * kernel version v (1: generic; 2: rhs block and epilogue fixed at compile
+ * time, for F32/BF16 batches with R = 8 or 16; 3: as 2, with the lattice rows
+ * staged in shared memory by bulk asynchronous copies issued by a producer
+ * warp, for Lx * R up to 384, falling back to 2 otherwise; 4: as 2 with one
+ * rhs per lane, a persistent grid whose CTAs take (rhs block, pass of sites)
+ * items round-robin so that the sites in flight form one compact front, and
+ * the loads of each hop issued while the previous hop computes), or 200 + b
+ * for the site traversal of versions 2 and 4 (b = 0 lexicographic, 1 4 x 4 x 2
+ * x 2 blocks when the extents are divisible, 2 z-half by z-half with t outermost
+ * within a half when Lz is even), or 300 + n to give version 3 n ring slots
+ * (2..6; 300: as many as fit), or 400 + h for the store hint of version 4 (h =
+ * 1: results stored with an L2 evict-first policy, 0: default); spc = sites per
+ * CTA (16..1024, power of two).  Values <= 0 keep the current setting.  Version 3 bounds every
  * wait for its staged rows; a wait that gives up makes the next call that
  * synchronises (a level, a solve, a reduction) return MMC_ERR_TIMEOUT. */
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc);
 /* The whole variant of one rhs-block class at once: rhs_class 0 for batches
  * whose block R is below 16 (up to 8 vectors, e.g. the solves of the M^-1
- * level), 1 for R = 16; version 1..3 (F64: 1), rpt 1 or 2, minb 1..8, spc as
- * above, blocked 0/1, ns 0 or 2..6.  MMC_ERR_ARG on any value out of range. */
+ * level), 1 for R = 16; version 1..4 (F64: 1), rpt 1 or 2, minb 1..8, spc as
+ * above, blocked = traversal 0..2, ns 0 or 2..6.  MMC_ERR_ARG on any value out
+ * of range.  The store hint of version 4 is set by mmc_set_step_variant. */
 int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int version, int rpt, int minb, int spc,
                                int blocked, int ns);
 /* Step chains (the degrees of a polynomial applied to a batch, Sec. 3, Sec. 5) run
@@ -402,11 +424,12 @@ int mmc_set_graphs(mmc_ctx* ctx, int enable);
  * launches (a capture the driver refused).  Context-owned string. */
 const char* mmc_graph_note(const mmc_ctx* ctx);
 /* Not part of the paper (launch tuning).  Autotuner: time every step-kernel
- * variant (M alone, without an epilogue) on an nrhs-vector field of
- * precision prec (random data, CUDA events, median of 3 after a warm-up),
- * keep the fastest for that precision and the rhs-block class of nrhs and
- * return it (best[6] = rpt, minb, spc, kernel version, blocked traversal, ring
- * slots of version 3) with its time per launch in ms. */
+ * variant on one degree of a polynomial level chain (M applied with the step
+ * update and the Z(4)-code bilinear epilogue, the form the Monte Carlo levels
+ * run) over an nrhs-vector noise field of precision prec (CUDA events, median
+ * of 3 after a warm-up), keep the fastest for that precision and the rhs-block
+ * class of nrhs and return it (best[6] = rpt, minb, spc, kernel version,
+ * traversal, ring slots of version 3) with its time per launch in ms. */
 int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms);
 
 /* Replace the device links by a new host field (same layout as mmc_load_gauge)
@@ -424,6 +447,27 @@ int mmc_harmonic_ritz(int m, const double* H, int ldh, double* theta_out);
 /* Leja ordering (Sec. 3) of m complex points: first the largest modulus, then
  * the maximiser of the product of distances (sum of logs), ties to lowest index. */
 int mmc_leja_order(int m, const double* theta_in, double* theta_out);
+/* Kept set of the deflation eigenpairs (Sec. 8: acceptance of Ritz pairs with
+ * residual below tol_accept; left vectors from gamma_5-hermiticity), the host
+ * rule mmc_deflate applies to its m candidates: lambda (2m doubles) and residual
+ * norms res (m).  The accepted ones, ordered by |lambda| (stable), the first k,
+ * are taken in that order: a real one (|Im| < 2e-4) is its own gamma_5 partner; a
+ * complex one takes the nearest candidate to its conjugate that is neither itself
+ * nor already taken, if closer than 10 max(2e-4, 1e-6 |lambda|), and is dropped
+ * otherwise.  keep, partner (m ints each, caller-owned) receive candidate indices,
+ * *n_keep their number.  Pure host. */
+int mmc_deflation_pairs(int m, const double* lambda, const double* res, double tol_accept, int k, int* keep,
+                        int* partner, int* n_keep);
+/* Drop rules of mmc_deflate on the q x q overlap S(i, j) = w_i^H z_j of the kept
+ * pairs (complex, column-major, leading dimension lds >= q), mates[i] = position
+ * of pair i's gamma_5 partner (i for a real eigenvalue): while S restricted to the
+ * selection is singular the last position is dropped, while a column of its
+ * inverse conjugate transpose (the size of a left vector u_i) has norm above
+ * max_u (mmc_deflate: 100) the position of the largest column is dropped; each
+ * drop takes the partner along.  sel (q ints) receives the kept positions in
+ * increasing order, *n_sel their number (0: nothing left).  Pure host. */
+int mmc_deflation_condition(int q, const double* S, int lds, const int* mates, double max_u, int* sel,
+                            int* n_sel);
 /* Eigenvalues (and right eigenvectors, column-major, if vr != NULL) of a complex
  * n x n matrix A (column-major, lda >= n); pure host FP64 (Hessenberg reduction
  * + shifted QR).  Used for the Ritz values of Sec. 3 and Sec. 7. */

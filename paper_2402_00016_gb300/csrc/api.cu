@@ -68,6 +68,7 @@ int mmc_destroy(mmc_ctx* ctx) {
   if (ctx->links32) cudaFree(ctx->links32);
   if (ctx->nbr) cudaFree(ctx->nbr);
   if (ctx->order) cudaFree(ctx->order);
+  if (ctx->order_zh) cudaFree(ctx->order_zh);
   if (ctx->step_err) cudaFree(ctx->step_err);
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
@@ -153,6 +154,24 @@ int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiod
     } else if (ctx->order) {
       cudaFree(ctx->order);
       ctx->order = nullptr;
+    }
+    // traversal z-half by z-half, each half t-major (t, z, y, x): the sites between a
+    // spinor's reads as a t+1 neighbour and as a t-1 neighbour are two t-slices of a
+    // half lattice, half of the lexicographic order's window
+    if (L[2] % 2 == 0 && L[2] >= 4) {
+      std::vector<int> ord;
+      ord.reserve(V);
+      const int hz = L[2] / 2;
+      for (int zh = 0; zh < 2; ++zh)
+        for (int t = 0; t < L[3]; ++t)
+          for (int z = zh * hz; z < (zh + 1) * hz; ++z)
+            for (int y = 0; y < L[1]; ++y)
+              for (int x = 0; x < L[0]; ++x) ord.push_back(x + L[0] * (y + L[1] * (z + L[2] * t)));
+      if (!ctx->order_zh) CK(cudaMalloc(&ctx->order_zh, ord.size() * sizeof(int)));
+      CK(cudaMemcpy(ctx->order_zh, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice));
+    } else if (ctx->order_zh) {
+      cudaFree(ctx->order_zh);
+      ctx->order_zh = nullptr;
     }
   }
   if (!ctx->links64) CK(cudaMalloc(&ctx->links64, h64.size() * sizeof(double2)));
@@ -241,13 +260,20 @@ int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner) {
 
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc) {
   if (!ctx || prec < 0 || prec > 2) return MMC_ERR_ARG;
-  if (minb >= 300) {  // minb = 300 + n: ring slots of the staged kernel (0: as many as fit)
+  if (minb >= 400) {  // minb = 400 + h: store hint of the fourth form (1: L2 evict-first)
+    const int h = minb - 400;
+    if (h < 0 || h > 1) RET(MMC_ERR_ARG, "store hint must be 0 or 1");
+    ctx->var_hint[prec][0] = ctx->var_hint[prec][1] = h;
+    minb = 0;
+  } else if (minb >= 300) {  // minb = 300 + n: ring slots of the staged kernel (0: as many as fit)
     const int n = minb - 300;
     if (n != 0 && (n < 2 || n > 6)) RET(MMC_ERR_ARG, "ring slots must be 2..6 (or 0)");
     ctx->var_ns[prec][0] = ctx->var_ns[prec][1] = n;
     minb = 0;
-  } else if (minb >= 200) {  // minb = 200 + b: traverse sites in 4D blocks (b = 1) or lexicographically (b = 0)
-    ctx->order_v[prec][0] = ctx->order_v[prec][1] = (minb - 200) != 0;
+  } else if (minb >= 200) {  // minb = 200 + b: traversal (0 lexicographic, 1 4D blocks, 2 z-halves)
+    const int b = minb - 200;
+    if (b < 0 || b > 2) RET(MMC_ERR_ARG, "traversal must be 0, 1 or 2");
+    ctx->order_v[prec][0] = ctx->order_v[prec][1] = b;
     minb = 0;
   } else if (minb >= 100) {  // minb = 100 + v selects kernel version v (1: generic, 2: compile-time rhs block)
     ctx->var_ver[prec][0] = ctx->var_ver[prec][1] = minb - 100;
@@ -282,7 +308,8 @@ const char* mmc_graph_note(const mmc_ctx* ctx) { return ctx ? ctx->graph_note.c_
 int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int version, int rpt, int minb, int spc,
                                int blocked, int ns) {
   if (!ctx || prec < 0 || prec > 2 || rhs_class < 0 || rhs_class > 1) return MMC_ERR_ARG;
-  if (version < 1 || version > 3 || (prec == MMC_F64 && version != 1)) RET(MMC_ERR_ARG, "bad kernel version");
+  if (version < 1 || version > 4 || (prec == MMC_F64 && version != 1)) RET(MMC_ERR_ARG, "bad kernel version");
+  if (blocked < 0 || blocked > 2) RET(MMC_ERR_ARG, "traversal must be 0, 1 or 2");
   if (rpt != 1 && rpt != 2) RET(MMC_ERR_ARG, "rpt must be 1 or 2");
   if (minb < 1 || minb > 8) RET(MMC_ERR_ARG, "minb must be 1..8");
   if (spc < 16 || spc > 1024 || (spc & (spc - 1))) RET(MMC_ERR_ARG, "spc must be a power of two in 16..1024");
@@ -291,7 +318,7 @@ int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int versio
   ctx->var_rpt[prec][rhs_class] = prec == MMC_F64 ? 1 : rpt;
   ctx->var_minb[prec][rhs_class] = minb;
   ctx->spc_v[prec][rhs_class] = spc;
-  ctx->order_v[prec][rhs_class] = blocked != 0;
+  ctx->order_v[prec][rhs_class] = blocked;
   ctx->var_ns[prec][rhs_class] = ns;
   return MMC_OK;
 }
@@ -301,18 +328,59 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   if (nrhs < 1 || prec < 0 || prec > 2) RET(MMC_ERR_ARG, "mmc_autotune: bad argument");
   cudaStream_t s = ctx->stream;
   geom g = make_geom(ctx, nrhs);
-  void *x, *y;
+  void *x, *y, *codes, *part;
   TRY(scratch(ctx, "tune_x", field_bytes(g, prec), &x));
   TRY(scratch(ctx, "tune_y", field_bytes(g, prec), &y));
+  TRY(scratch(ctx, "tune_codes", size_t(g.npad) * g.V * sizeof(uint32_t), &codes));
+  const int nbx = nbx_step(ctx);
+  TRY(scratch(ctx, "tune_part", size_t(nbx) * g.npad * sizeof(double2), &part));
   std::vector<uint2> ids(g.npad);
   for (int r = 0; r < g.npad; ++r) ids[r] = make_uint2(7u, uint32_t(r));
   void* dids;
   TRY(scratch(ctx, "ids", ids.size() * sizeof(uint2), &dids));
   CK(cudaMemcpyAsync(dids, ids.data(), ids.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
-  CK(mmc::launch_noise(prec, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, x, nullptr, s));
+  CK(mmc::launch_noise(prec, g, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, x, (uint32_t*)codes, s));
+  CK(cudaMemsetAsync(part, 0, size_t(nbx) * g.npad * sizeof(double2), s));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // The timed launch is one degree of a polynomial level chain, the form the levels
+  // spend their time in: y = (1 - 1/t) x + (kappa/t) D x with the Z(4)-code bilinear
+  // of x accumulated (the step kernel's epilogue decides its cost as much as the hop).
+  Run run;
+  run.g = g;
+  run.prec = prec;
+  run.codes = (const uint32_t*)codes;
+  run.partial = (double2*)part;
+  run.nbx = nbx;
+  {
+    Step st;
+    st.in = x;
+    st.out = y;
+    st.flags = mmc::SF_HOP | mmc::SF_WRITE | mmc::SF_BIL_CODES;
+    st.coef = coef_block(g.npad);
+    const cd it(0.8, 0.3);
+    for (int r = 0; r < g.npad; ++r) set_coef(st.coef, g.npad, r, 1.0 - it, ctx->kappa * it, 0, it, 0);
+    run.steps.push_back(st);
+  }
+  float med = 0;
+  auto time_variant = [&]() -> int {
+    TRY(exec_run(ctx, run, s));
+    std::vector<float> t;
+    for (int rep = 0; rep < 3; ++rep) {
+      CK(cudaEventRecord(e0, s));
+      TRY(exec_run(ctx, run, s));
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      t.push_back(ms);
+    }
+    TRY(check_step_err(ctx, s));
+    std::sort(t.begin(), t.end());
+    med = t[1];
+    return MMC_OK;
+  };
   const int rpts[2] = {1, 2};
   const int minbs[3] = {1, 3, 4};
   const int minbs2[2] = {4, 6};  // v2, one rhs per lane: 128 or 80 registers
@@ -321,11 +389,12 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   const int rc = rclass(g.R);  // the variant is kept for this rhs-block class only
   int br = ctx->var_rpt[prec][rc], bm = ctx->var_minb[prec][rc], bs = ctx->spc_v[prec][rc], bv = ctx->var_ver[prec][rc];
   const bool v2ok = prec != MMC_F64 && (g.R == 8 || g.R == 16);
-  bool bo = ctx->order_v[prec][rc];
-  for (int ordr = 0; ordr <= ((v2ok && ctx->order) ? 1 : 0); ++ordr)
+  int bo = ctx->order_v[prec][rc];
+  for (int ordr = 0; ordr <= (v2ok ? 2 : 0); ++ordr)
   for (int ver = 1; ver <= (v2ok ? 2 : 1); ++ver)
   for (int ri = 0; ri < 2; ++ri) {
-    if (ordr == 1 && ver == 1) continue;  // the blocked traversal exists in the v2 kernel only
+    if (ordr > 0 && ver == 1) continue;  // the traversal orders exist in the v2 and v4 kernels only
+    if ((ordr == 1 && !ctx->order) || (ordr == 2 && !ctx->order_zh)) continue;
     if (prec == MMC_F64 && rpts[ri] != 1) continue;
     if (rpts[ri] > g.R) continue;
     const int nmb = ver == 1 ? 3 : (rpts[ri] == 1 ? 2 : 1);  // v2 with two rhs per lane has one cap
@@ -335,34 +404,23 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
         ctx->var_ver[prec][rc] = ver;
         ctx->var_rpt[prec][rc] = rpts[ri];
         ctx->var_minb[prec][rc] = mbv;
-        ctx->order_v[prec][rc] = ordr == 1;
+        ctx->order_v[prec][rc] = ordr;
         ctx->spc_v[prec][rc] = spcs[si];
-        TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
-        std::vector<float> t;
-        for (int rep = 0; rep < 3; ++rep) {
-          CK(cudaEventRecord(e0, s));
-          TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
-          CK(cudaEventRecord(e1, s));
-          CK(cudaEventSynchronize(e1));
-          float ms;
-          CK(cudaEventElapsedTime(&ms, e0, e1));
-          t.push_back(ms);
-        }
-        std::sort(t.begin(), t.end());
-        if (t[1] < best_ms) {
-          best_ms = t[1];
+        TRY(time_variant());
+        if (med < best_ms) {
+          best_ms = med;
           br = rpts[ri];
           bm = mbv;
           bs = spcs[si];
           bv = ver;
-          bo = ordr == 1;
+          bo = ordr;
         }
       }
     }
   }
-  // the staged form (version 3) with its ring depths; rpt, caps and traversal do not apply
   int bn = ctx->var_ns[prec][rc];
   if (v2ok) {
+    // the staged form (version 3) with its ring depths; rpt, caps and traversal do not apply
     const int nss[3] = {0, 2, 4};
     for (int ri = 0; ri < 2; ++ri)
     for (int ni = 0; ni < 3; ++ni) {
@@ -370,26 +428,31 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
       ctx->var_ver[prec][rc] = 3;
       ctx->var_ns[prec][rc] = nss[ni];
       ctx->var_rpt[prec][rc] = rpts[ri];
-      ctx->order_v[prec][rc] = false;
-      TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
-      std::vector<float> t;
-      for (int rep = 0; rep < 3; ++rep) {
-        CK(cudaEventRecord(e0, s));
-        TRY(apply_M_impl(ctx, x, y, nrhs, prec, false, s));
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        float ms;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        t.push_back(ms);
-      }
-      TRY(check_step_err(ctx, s));
-      std::sort(t.begin(), t.end());
-      if (t[1] < best_ms) {
-        best_ms = t[1];
+      ctx->order_v[prec][rc] = 0;
+      TRY(time_variant());
+      if (med < best_ms) {
+        best_ms = med;
         bv = 3;
         bn = nss[ni];
         br = rpts[ri];
-        bo = false;
+        bo = 0;
+      }
+    }
+    // the persistent, pipelined form (version 4, one rhs per lane): register caps and traversals
+    for (int ordr = 0; ordr <= 2; ++ordr)
+    for (int mb = 3; mb <= 4; ++mb) {
+      if ((ordr == 1 && !ctx->order) || (ordr == 2 && !ctx->order_zh)) continue;
+      ctx->var_ver[prec][rc] = 4;
+      ctx->var_rpt[prec][rc] = 1;
+      ctx->var_minb[prec][rc] = mb;
+      ctx->order_v[prec][rc] = ordr;
+      TRY(time_variant());
+      if (med < best_ms) {
+        best_ms = med;
+        bv = 4;
+        br = 1;
+        bm = mb;
+        bo = ordr;
       }
     }
   }
@@ -406,7 +469,7 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
     best[1] = bm;
     best[2] = bs;
     best[3] = bv;
-    best[4] = bo ? 1 : 0;
+    best[4] = bo;
     best[5] = bn;
   }
   if (ms_out) *ms_out = best_ms;
@@ -584,6 +647,39 @@ int mmc_leja_order(int m, const double* in, double* out) {
     out[2 * i] = p[i].real();
     out[2 * i + 1] = p[i].imag();
   }
+  return MMC_OK;
+}
+
+int mmc_deflation_pairs(int m, const double* lambda, const double* res, double tol_accept, int k, int* keep,
+                        int* partner, int* n_keep) {
+  if (m < 0 || k < 0 || !n_keep || (m > 0 && (!lambda || !res || !keep || !partner))) return MMC_ERR_ARG;
+  std::vector<cd> l(m);
+  std::vector<double> r(res, res + m);
+  for (int i = 0; i < m; ++i) l[i] = cd(lambda[2 * i], lambda[2 * i + 1]);
+  std::vector<int> kp, pt;
+  mmc::deflation_pairs(l, r, tol_accept, k, 2e-4, kp, pt);
+  *n_keep = int(kp.size());
+  for (size_t i = 0; i < kp.size(); ++i) {
+    keep[i] = kp[i];
+    partner[i] = pt[i];
+  }
+  return MMC_OK;
+}
+
+int mmc_deflation_condition(int q, const double* S, int lds, const int* mates, double max_u, int* sel,
+                            int* n_sel) {
+  if (q < 0 || !n_sel || (q > 0 && (!S || !mates || !sel || lds < q))) return MMC_ERR_ARG;
+  CMat M(q, q);
+  std::vector<int> mt(mates, mates + q);
+  for (int i = 0; i < q; ++i)
+    if (mt[i] < 0 || mt[i] >= q) return MMC_ERR_ARG;
+  for (int j = 0; j < q; ++j)
+    for (int i = 0; i < q; ++i) M(i, j) = cd(S[2 * (i + size_t(j) * lds)], S[2 * (i + size_t(j) * lds) + 1]);
+  std::vector<int> sl;
+  CMat Inv;
+  mmc::deflation_condition(M, mt, max_u, sl, Inv);
+  *n_sel = int(sl.size());
+  for (size_t i = 0; i < sl.size(); ++i) sel[i] = sl[i];
   return MMC_OK;
 }
 

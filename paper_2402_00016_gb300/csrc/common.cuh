@@ -41,6 +41,7 @@ struct step_params {
   int* err;                // device flag: set by a kernel whose bounded wait gave up (staged form)
   long long wait_iters;    // bound of each mbarrier wait of the staged form (0: the default)
   int stall_test;          // fault injection: the staged form's producer issues no copies
+  int hint;                // bit 0: store the result with an L2 evict-first policy (fourth form)
 };
 
 template <typename T>

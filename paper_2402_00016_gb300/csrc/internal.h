@@ -88,6 +88,7 @@ struct mmc_ctx {
   long long graph_launches0 = 0;      // value at the last mmc_profile(ctx, 1)
   long long graph_captures = 0, graph_captures0 = 0;
   std::string graph_note;             // why graphs were switched off, if they were
+  double defl_max_u = 100.0;  // mmc_deflate: bound on the norm of a left vector u_i (a column of (W^H Z)^{-H})
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
   long long wait_iters = 0;   // bound of the staged kernel's mbarrier waits (0: its default)
@@ -105,7 +106,10 @@ struct mmc_ctx {
   int* step_err = nullptr;     // device flag of the staged step kernel's bounded waits
   int* nbr = nullptr;          // device neighbour table [site][8]
   int* order = nullptr;        // device traversal order in 4D blocks (null if the extents do not allow it)
-  bool order_v[3][2] = {{false, false}, {false, false}, {false, false}};  // 4D-blocked traversal (v2)
+  int* order_zh = nullptr;     // device traversal order z-half by z-half, t-major within a half (null if Lz is odd)
+  // traversal of the step kernel (versions 2, 4): 0 lexicographic, 1 4D blocks, 2 z-halves
+  int order_v[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  int var_hint[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // store hint of the fourth form (bit 0: L2 evict-first)
   // profiling (mmc_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -314,7 +318,8 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       p.links = run.prec == MMC_F64 ? ctx->links64 : ctx->links32;
       p.rb_len = run.rb_len;
       p.nbr = ctx->nbr;
-      p.order = ctx->order_v[run.prec][rc] ? ctx->order : nullptr;
+      p.order = ctx->order_v[run.prec][rc] == 1 ? ctx->order : ctx->order_v[run.prec][rc] == 2 ? ctx->order_zh : nullptr;
+      p.hint = ctx->var_hint[run.prec][rc];
       p.step = int(k);
       p.V = ctx->V;
       p.R = g.R;
@@ -338,7 +343,15 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
         CK(cudaEventRecord(e0, s));
       }
       bool done = false;
-      if (ctx->var_ver[run.prec][rc] == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      if (ctx->var_ver[run.prec][rc] == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+        cudaError_t e4 = cudaSuccess;
+        const int mb = ctx->var_minb[run.prec][rc] == 3 ? 3 : 4;
+        const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
+        done = run.prec == MMC_F32 ? mmc::launch_step4_f32(g.R, mb, p, g.nrb, nbx, s, &e4)
+                                   : mmc::launch_step4_bf16(g.R, mb, p, g.nrb, nbx, s, &e4);
+        CK(e4);
+      }
+      if (!done && ctx->var_ver[run.prec][rc] == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e3 = cudaSuccess;
         done = mmc::launch_step3(run.prec, g.R, rpt, run.nbx, ctx->var_ns[run.prec][rc], p, g.nrb, s, &e3);
         CK(e3);
@@ -382,7 +395,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     mix(uint64_t(ctx->wait_iters));
     mix(uint64_t(ctx->var_ver[run.prec][rc]) | (uint64_t(rpt) << 8) | (uint64_t(ctx->var_minb[run.prec][rc]) << 16) |
         (uint64_t(ctx->spc_v[run.prec][rc]) << 24) | (uint64_t(ctx->order_v[run.prec][rc]) << 40) |
-        (uint64_t(ctx->var_ns[run.prec][rc]) << 48));
+        (uint64_t(ctx->var_ns[run.prec][rc]) << 48) | (uint64_t(ctx->var_hint[run.prec][rc]) << 56));
     for (const Step& st : run.steps) {
       mix(reinterpret_cast<uintptr_t>(st.in));
       mix(reinterpret_cast<uintptr_t>(st.out));
@@ -447,16 +460,19 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     const Step& st = run.steps[k];
     if (prof) {
       ctx->prof_launches += 1;
-      // algorithmic bytes and flops of this launch (all rhs blocks active)
+      // algorithmic bytes and flops of this launch (all rhs blocks active), the bytes
+      // at ideal reuse: every input, output, aux, accumulator and left-field element
+      // once, the 4 links of a site (9 complex each, no padding) once for the whole
+      // batch, and nothing for the Z(4) noise of the code bilinear (it could be
+      // regenerated from the counter-based generator instead of read)
       const double sb = double(elem_bytes(run.prec)) * 12;  // one spinor, one rhs
       const double per_rhs = sb * ((st.flags & mmc::SF_HOP) ? 2 : 1) * ((st.flags & mmc::SF_WRITE) ? 1 : 0) +
                              (((st.flags & mmc::SF_WRITE) == 0) ? sb : 0.0) +
                              ((st.flags & mmc::SF_AUX) ? sb : 0.0) +
                              ((st.flags & mmc::SF_YACC) ? 2.0 * 12 * (run.prec == MMC_F64 ? 16 : 8) : 0.0) +
-                             ((st.flags & mmc::SF_BIL_CODES) ? 4.0 : 0.0) +
                              ((st.flags & mmc::SF_BIL_LEFT) ? sb : 0.0);
       const double links = (st.flags & mmc::SF_HOP) ? 4.0 * 9 * (run.prec == MMC_F64 ? 16 : 8) : 0.0;
-      ctx->prof_bytes += double(ctx->V) * (double(g.npad) * per_rhs + double(g.nrb) * links);
+      ctx->prof_bytes += double(ctx->V) * (double(g.npad) * per_rhs + links);
       ctx->prof_flops += double(ctx->V) * g.npad * (((st.flags & mmc::SF_HOP) ? 1368.0 : 0.0) + 48.0);
     }
     if (st.flags & mmc::SF_HOP) ctx->matvecs += g.npad;

@@ -25,6 +25,12 @@ cudaError_t launch_step(int prec, int rpt, int minb, const step_params& p, int n
 // minb (RPT = 1 only): 6 caps registers at 80 (24 warps per SM), else 128 (16 warps).
 bool launch_step2_f32(int R, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
 bool launch_step2_bf16(int R, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
+// Fourth form (stencil4.cuh): persistent grid over (rhs block, site pass) items with a
+// compact front, loads of the next hop issued before the current hop's products; one
+// rhs per lane, R = 8 or 16; minb 3 (168 registers) or 4 (128).  nbx: rows of the
+// bilinear partials.  Returns false when the flags need another form.
+bool launch_step4_f32(int R, int minb, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err);
+bool launch_step4_bf16(int R, int minb, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err);
 // Staged form (rows by bulk asynchronous copies, stencil3.cuh) for FP32 (prec 1) and BF16
 // (prec 2) storage, R = 8 or 16, rpt = 1 or 2 rhs per thread; nbx: rows of the bilinear
 // partials (grid bound), ns: ring slots (0: as many as fit).  Returns false when the

@@ -5,6 +5,7 @@
 // by someone else (a framework's caching allocator that holds the GPU's
 // memory, a service with a fixed memory budget that forbids allocation once it
 // is running).  The caller still passes the output field.
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -17,10 +18,14 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint2 g_noise_ids[kNoallocMaxRhs];
 
-// Device address of g_noise_ids per device, looked up once per device.  In host
-// code the name g_noise_ids is only a host-side stand-in for the symbol, so the
-// kernel must be given this address, never the name.
+// Device address of g_noise_ids per device, looked up once per device (under a
+// std::call_once per device, so host threads making their first call on the same
+// device at the same time do not race).  In host code the name g_noise_ids is only
+// a host-side stand-in for the symbol, so the kernel must be given this address,
+// never the name.
 uint2* g_ids_addr[kMaxDevices] = {};
+cudaError_t g_ids_err[kMaxDevices] = {};
+std::once_flag g_ids_once[kMaxDevices];
 
 }  // namespace
 
@@ -33,12 +38,14 @@ extern "C" int mmc_noise_noalloc(mmc_ctx* ctx, uint32_t level, uint32_t first, u
                          " right-hand sides (padded to the rhs block); use mmc_noise for larger batches");
   if (ctx->device < 0 || ctx->device >= kMaxDevices) RET(MMC_ERR_ARG, "mmc_noise_noalloc: device index out of range");
   CK(cudaSetDevice(ctx->device));
-  if (!g_ids_addr[ctx->device]) {
+  const int dev = ctx->device;
+  std::call_once(g_ids_once[dev], [dev] {
     void* p = nullptr;
-    CK(cudaGetSymbolAddress(&p, g_noise_ids));  // with ctx->device current
-    g_ids_addr[ctx->device] = static_cast<uint2*>(p);
-  }
-  uint2* ids_dev = g_ids_addr[ctx->device];
+    g_ids_err[dev] = cudaGetSymbolAddress(&p, g_noise_ids);  // with device `dev` current
+    if (g_ids_err[dev] == cudaSuccess) g_ids_addr[dev] = static_cast<uint2*>(p);
+  });
+  CK(g_ids_err[dev]);
+  uint2* ids_dev = g_ids_addr[dev];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // every entry the kernel reads is rewritten here: nothing is left from an earlier call
   std::vector<uint2> ids(g.npad);

@@ -1,0 +1,427 @@
+// Fused Wilson step kernel, fourth form (same arithmetic and operand conventions
+// as step_kernel and step2_kernel: out = a in + b D in + g aux with the epilogues
+// of step_params).  Two changes against the second form, both aimed at the HBM
+// roofline of the stencil:
+//
+//  * A persistent grid (one wave of resident CTAs) takes work items round-robin.
+//    An item is one pass of SPP sites of one rhs block; items run rhs block by
+//    rhs block and, within a block, in site traversal order.  The sites in flight
+//    on the whole GPU therefore form one compact front of (CTAs x SPP) sites that
+//    advances through the lattice, so a spinor read as the t+1 neighbour is still
+//    in L2 when it is read again as its own site and as the t-1 neighbour (about
+//    two t-slices of one rhs block later) instead of being evicted by the reads of
+//    CTAs spread over several slices.
+//  * Software pipelining over the eight hops: the neighbour spinor and link of hop
+//    d+1 are loaded while hop d does its SU(3) products, and the own site's spinor
+//    while the last hop computes; the second form waits for every hop's loads.
+//
+// Optionally (p.hint & 1) the result is stored with an L2 evict-first policy: it is
+// not read again by this launch, so L2 keeps the inputs instead.
+#pragma once
+#include <algorithm>
+
+#include "kernels.h"
+#include "stencil_ops.cuh"
+
+namespace mmc {
+namespace sten4 {
+using namespace sten;
+
+enum Acc { ACC_NONE = 0, ACC_CODES = 1, ACC_Y = 2, ACC_LEFT = 3 };
+
+// the 12 spin-colour components of a site for RPT right-hand sides
+template <typename S, int R, int RPT>
+__device__ __forceinline__ void load_spinor(const S* p, cx<typename StoreTraits<S>::R> (&v)[12][RPT]) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) load_rpt<S, RPT>(p + c * R, v[c]);
+}
+
+// upper half-spinor h = P psi of the projector (1 - sg gamma_MU) in the chiral basis
+template <typename T, int RPT, int MU, int SG>
+__device__ __forceinline__ void project(const cx<T> (&s)[12][RPT], cx<T> (&h0)[3][RPT], cx<T> (&h1)[3][RPT]) {
+  const T sg = SG;
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      const cx<T> s0 = s[b][j], s1 = s[3 + b][j], s2 = s[6 + b][j], s3 = s[9 + b][j];
+      if (MU == 0) {
+        h0[b][j] = cadd(s0, cscale(ctimes_i(s3), sg));
+        h1[b][j] = cadd(s1, cscale(ctimes_i(s2), sg));
+      } else if (MU == 1) {
+        h0[b][j] = cadd(s0, cscale(s3, sg));
+        h1[b][j] = csub(s1, cscale(s2, sg));
+      } else if (MU == 2) {
+        h0[b][j] = cadd(s0, cscale(ctimes_i(s2), sg));
+        h1[b][j] = csub(s1, cscale(ctimes_i(s3), sg));
+      } else {
+        h0[b][j] = csub(s0, cscale(s2, sg));
+        h1[b][j] = csub(s1, cscale(s3, sg));
+      }
+    }
+}
+
+// acc += (1 - sg gamma_MU) W h with W = U (DAGU false) or U^+ (DAGU true): the colour
+// products of the two upper components and the lower half rebuilt from them
+template <typename T, int RPT, int MU, bool DAGU, int SG>
+__device__ __forceinline__ void multiply_add(const Link<T>& L, const cx<T> (&h0)[3][RPT], const cx<T> (&h1)[3][RPT],
+                                             cx<T> (&acc)[12][RPT]) {
+  const T sg = SG;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      cx<T> v0 = cmake(T(0), T(0)), v1 = cmake(T(0), T(0));
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (DAGU) {
+          v0 = cfmac(L.u[b * 3 + a], h0[b][j], v0);
+          v1 = cfmac(L.u[b * 3 + a], h1[b][j], v1);
+        } else {
+          v0 = cfma(L.u[a * 3 + b], h0[b][j], v0);
+          v1 = cfma(L.u[a * 3 + b], h1[b][j], v1);
+        }
+      }
+      cx<T> r2, r3;
+      if (MU == 0) {
+        r2 = cscale(ctimes_i(v1), -sg);
+        r3 = cscale(ctimes_i(v0), -sg);
+      } else if (MU == 1) {
+        r2 = cscale(v1, -sg);
+        r3 = cscale(v0, sg);
+      } else if (MU == 2) {
+        r2 = cscale(ctimes_i(v0), -sg);
+        r3 = cscale(ctimes_i(v1), sg);
+      } else {
+        r2 = cscale(v0, -sg);
+        r3 = cscale(v1, -sg);
+      }
+      acc[a][j] = cadd(acc[a][j], v0);
+      acc[3 + a][j] = cadd(acc[3 + a][j], v1);
+      acc[6 + a][j] = cadd(acc[6 + a][j], r2);
+      acc[9 + a][j] = cadd(acc[9 + a][j], r3);
+    }
+}
+
+// compiler fences (see fence_acc) on the accumulators and on a pair of half-spinors
+template <typename T, int RPT>
+__device__ __forceinline__ void fence_arr(cx<T> (&v)[12][RPT]) {
+#pragma unroll
+  for (int c = 0; c < 12; c += 2)
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) fence_acc(v[c][j].re, v[c][j].im, v[c + 1][j].re, v[c + 1][j].im);
+}
+template <typename T, int RPT>
+__device__ __forceinline__ void fence_half(cx<T> (&h0)[3][RPT], cx<T> (&h1)[3][RPT]) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) fence_acc(h0[b][j].re, h0[b][j].im, h1[b][j].re, h1[b][j].im);
+}
+
+// stores, optionally with an L2 evict-first cache policy
+template <typename S, int RPT>
+__device__ __forceinline__ void store_hint(S* p, const cx<typename StoreTraits<S>::R> (&v)[RPT], bool ef,
+                                           uint64_t pol) {
+  if (!ef) {
+    store_rpt<S, RPT>(p, v);
+    return;
+  }
+  S tmp[RPT];
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) from_cx(v[j], tmp[j]);
+  if constexpr (sizeof(S) * RPT == 16) {
+    const uint4 w = *reinterpret_cast<const uint4*>(tmp);
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "r"(w.x), "r"(w.y), "r"(w.z),
+                 "r"(w.w), "l"(pol)
+                 : "memory");
+  } else if constexpr (sizeof(S) * RPT == 8) {
+    const uint2 w = *reinterpret_cast<const uint2*>(tmp);
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1,%2}, %3;" ::"l"(p), "r"(w.x), "r"(w.y), "l"(pol)
+                 : "memory");
+  } else if constexpr (sizeof(S) * RPT == 4) {
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(tmp);
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(w), "l"(pol) : "memory");
+  } else {
+    store_rpt<S, RPT>(p, v);
+  }
+}
+
+// Hop D of the eight (0: x+, 1: x-, 2: y+, ..., 7: t-): project the spinor in `sp`,
+// start the loads of hop D+1 (or, after the last hop, of the own site) into `sp`
+// and `lk`, then multiply with the link of hop D and accumulate.
+// LATE: load the next link after the products (18 registers fewer, its latency not hidden).
+template <typename S, int R, int RPT, int KD, int D, bool LATE>
+__device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in, int site, const int4& nf,
+                                              const int4& nb, cx<typename StoreTraits<S>::R> (&sp)[12][RPT],
+                                              Link<typename StoreTraits<S>::R>& lk,
+                                              cx<typename StoreTraits<S>::R> (&acc)[12][RPT]) {
+  using T = typename StoreTraits<S>::R;
+  constexpr int MU = D / 2;
+  constexpr bool BWD = (D & 1) != 0;
+  constexpr int SG = BWD ? -KD : KD;
+  cx<T> h0[3][RPT], h1[3][RPT];
+  project<T, RPT, MU, SG>(sp, h0, h1);
+  fence_half<T, RPT>(h0, h1);
+  constexpr int NMU = (D + 1) / 2;
+  constexpr bool NBWD = ((D + 1) & 1) != 0;
+  const int nsite = D == 7 ? site
+                           : NBWD ? (NMU == 0 ? nb.x : NMU == 1 ? nb.y : NMU == 2 ? nb.z : nb.w)
+                                  : (NMU == 0 ? nf.x : NMU == 1 ? nf.y : NMU == 2 ? nf.z : nf.w);
+  if constexpr (LATE) {
+    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
+    multiply_add<T, RPT, MU, BWD, SG>(lk, h0, h1, acc);
+    fence_arr<T, RPT>(acc);
+    if constexpr (D < 7) load_link(p.links, NBWD ? nsite : site, NMU, lk);
+  } else {
+    const Link<T> lc = lk;
+    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);
+    if constexpr (D < 7) load_link(p.links, NBWD ? nsite : site, NMU, lk);
+    multiply_add<T, RPT, MU, BWD, SG>(lc, h0, h1, acc);
+    fence_arr<T, RPT>(acc);
+  }
+}
+
+// TH: the insertion Theta of the code bilinear when fixed at compile time (0: the
+// identity), -1 when read from p.theta.
+template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH>
+__global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_chunks, int n_items) {
+  using T = float;
+  constexpr int L = R / RPT;    // lanes per site
+  constexpr int SPP = 128 / L;  // sites per item
+  constexpr bool BIL = (ACC == ACC_CODES || ACC == ACC_LEFT);
+  const int lane = threadIdx.x % L;
+  const int r0 = lane * RPT;
+  const bool bil_out = (p.flags & SF_BIL_OUT) != 0;
+  const bool ef = (p.hint & 1) != 0;
+  uint64_t pol = 0;
+  if (ef) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  __shared__ double2 red[4][32];
+  const int warp = threadIdx.x >> 5;
+  const int wl = threadIdx.x & 31;
+
+  cx<T> ca[RPT], cb[RPT], cg[RPT], cwi[RPT], cwo[RPT];
+  double bre[RPT], bim[RPT];
+  int cur_rb = -1;
+
+  // bilinear sums of this CTA for rhs block rb into its partial row (block-uniform call)
+  auto flush = [&](int rb) {
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+#pragma unroll
+      for (int off = L; off < 32; off <<= 1) {
+        bre[j] += __shfl_xor_sync(0xffffffffu, bre[j], off);
+        bim[j] += __shfl_xor_sync(0xffffffffu, bim[j], off);
+      }
+    }
+    if (wl < L) {
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) red[warp][wl * RPT + j] = make_double2(bre[j], bim[j]);
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+      double sr = 0, sim = 0;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        sr += red[w][threadIdx.x].x;
+        sim += red[w][threadIdx.x].y;
+      }
+      double2* dst = p.partial + size_t(blockIdx.x) * p.npad + rb * R + threadIdx.x;
+      double2 cur = *dst;
+      cur.x += sr;
+      cur.y += sim;
+      *dst = cur;
+    }
+    __syncthreads();
+  };
+
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int rb = item / n_chunks;
+    if (rb != cur_rb) {  // uniform over the CTA: every thread takes the same items
+      if (BIL && cur_rb >= 0) flush(cur_rb);
+      cur_rb = rb;
+      const int rglob = rb * R + r0;
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        double2 v;
+        v = p.coef[0 * p.npad + rglob + j];
+        ca[j] = cmake(T(v.x), T(v.y));
+        v = p.coef[1 * p.npad + rglob + j];
+        cb[j] = cmake(T(v.x), T(v.y));
+        if (AUX) {
+          v = p.coef[2 * p.npad + rglob + j];
+          cg[j] = cmake(T(v.x), T(v.y));
+        }
+        if (ACC != ACC_NONE) {
+          v = p.coef[3 * p.npad + rglob + j];
+          cwi[j] = cmake(T(v.x), T(v.y));
+          v = p.coef[4 * p.npad + rglob + j];
+          cwo[j] = cmake(T(v.x), T(v.y));
+        }
+        bre[j] = bim[j] = 0.0;
+      }
+    }
+    if (p.rb_len && p.step >= p.rb_len[rb]) continue;
+    const int pos = (item - rb * n_chunks) * SPP + threadIdx.x / L;
+    if (pos >= p.V) continue;
+    const size_t rb_off = size_t(rb) * p.V * 12 * R;
+    const S* in = reinterpret_cast<const S*>(p.in) + rb_off + r0;
+    const int site = p.order ? __ldg(p.order + pos) : pos;
+    const int4 nf = __ldg(reinterpret_cast<const int4*>(p.nbr) + 2 * size_t(site));
+    const int4 nb = __ldg(reinterpret_cast<const int4*>(p.nbr) + 2 * size_t(site) + 1);
+    uint32_t code[RPT];
+    if (ACC == ACC_CODES) {
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) code[j] = __ldg(p.codes + (size_t(rb) * p.V + site) * R + r0 + j);
+    }
+    cx<T> acc[12][RPT];
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) acc[c][j] = cmake(T(0), T(0));
+    cx<T> sp[12][RPT];
+    Link<T> lk;
+    load_spinor<S, R, RPT>(in + size_t(nf.x) * 12 * R, sp);
+    load_link(p.links, site, 0, lk);
+    hop_pipelined<S, R, RPT, KD, 0, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
+    hop_pipelined<S, R, RPT, KD, 1, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
+    hop_pipelined<S, R, RPT, KD, 2, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
+    hop_pipelined<S, R, RPT, KD, 3, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
+    hop_pipelined<S, R, RPT, KD, 4, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
+    hop_pipelined<S, R, RPT, KD, 5, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
+    hop_pipelined<S, R, RPT, KD, 6, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
+    hop_pipelined<S, R, RPT, KD, 7, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);  // leaves the own spinor in sp
+
+    const size_t boff = rb_off + size_t(site) * 12 * R + r0;
+    cx<T> si[RPT], so[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) si[j] = so[j] = cmake(T(0), T(0));
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      cx<T> vout[RPT];
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) vout[j] = cfma(cb[j], acc[c][j], cmul(ca[j], sp[c][j]));
+      if (AUX) {
+        cx<T> ax[RPT];
+        load_rpt<S, RPT>(reinterpret_cast<const S*>(p.aux) + boff + c * R, ax);
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], ax[j], vout[j]);
+      }
+      store_hint<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout, ef, pol);
+      if (ACC == ACC_Y) {
+        float2* yp = reinterpret_cast<float2*>(p.y) + boff + c * R;
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+          float2 yv = yp[j];
+          cx<T> a = cmake(yv.x, yv.y);
+          a = cfma(cwi[j], sp[c][j], a);
+          if (bil_out) a = cfma(cwo[j], vout[j], a);
+          yp[j] = make_float2(a.re, a.im);
+        }
+      }
+      if (BIL) {
+        const int theta = TH >= 0 ? TH : p.theta;
+        const int cp = (theta == 1) ? (c + 6) % 12 : c;
+        const T sg = (theta == 2 && c >= 6) ? T(-1) : T(1);
+        if (ACC == ACC_CODES) {
+          // conj(i^k) v: k odd swaps (re, im) -> (im, -re), k >= 2 negates (gamma_5 sign folded in)
+#pragma unroll
+          for (int j = 0; j < RPT; ++j) {
+            const uint32_t k = (code[j] >> (2 * cp)) & 3u;
+            const T f = (k & 2u) ? -sg : sg;
+            const bool odd = (k & 1u) != 0;
+            si[j].re = fmaf(f, odd ? sp[c][j].im : sp[c][j].re, si[j].re);
+            si[j].im = fmaf(f, odd ? -sp[c][j].re : sp[c][j].im, si[j].im);
+            if (bil_out) {
+              so[j].re = fmaf(f, odd ? vout[j].im : vout[j].re, so[j].re);
+              so[j].im = fmaf(f, odd ? -vout[j].re : vout[j].im, so[j].im);
+            }
+          }
+        } else {
+          cx<T> eta[RPT];
+          load_rpt<S, RPT>(reinterpret_cast<const S*>(p.left) + boff + size_t(cp) * R, eta);
+#pragma unroll
+          for (int j = 0; j < RPT; ++j) {
+            si[j] = cfmac(eta[j], cscale(sp[c][j], sg), si[j]);
+            if (bil_out) so[j] = cfmac(eta[j], cscale(vout[j], sg), so[j]);
+          }
+        }
+      }
+    }
+    if (BIL) {
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        cx<T> contrib = cmul(cwi[j], si[j]);
+        if (bil_out) contrib = cfma(cwo[j], so[j], contrib);
+        bre[j] += double(contrib.re);
+        bim[j] += double(contrib.im);
+      }
+    }
+  }
+  if (BIL && cur_rb >= 0) flush(cur_rb);
+}
+
+template <typename K>
+inline int resident_ctas(K kern) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm;
+}
+
+// Dispatch of one (S, R) family over the epilogue modes (one rhs per lane); false
+// when the flags need another form.  nbx: rows of the bilinear partials (grid bound).
+template <typename S, int R, int MINB>
+bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err) {
+  constexpr int RPT = 1;
+  const int f = p.flags;
+  if (!(f & SF_HOP) || !(f & SF_WRITE)) return false;
+  const bool aux = (f & SF_AUX) != 0;
+  int acc = ACC_NONE;
+  if (f & SF_BIL_CODES) acc = ACC_CODES;
+  else if (f & SF_YACC) acc = ACC_Y;
+  else if (f & SF_BIL_LEFT) acc = ACC_LEFT;
+  if ((f & SF_DAGGER) && (aux || acc != ACC_NONE)) return false;
+  void (*kern)(step_params, int, int) = nullptr;
+  if (f & SF_DAGGER) {
+    kern = step4_kernel<S, R, RPT, MINB, -1, false, ACC_NONE, -1>;
+  } else if (!aux) {
+    switch (acc) {
+      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_NONE, -1>; break;
+      case ACC_CODES:
+        kern = p.theta == 0 ? step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, 0>
+                            : step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, -1>;
+        break;
+      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_Y, -1>; break;
+      default: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_LEFT, -1>; break;
+    }
+  } else {
+    switch (acc) {
+      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_NONE, -1>; break;
+      case ACC_CODES: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_CODES, -1>; break;
+      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_Y, -1>; break;
+      default: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_LEFT, -1>; break;
+    }
+  }
+  constexpr int SPP = 128 / (R / RPT);
+  const int n_chunks = (p.V + SPP - 1) / SPP;
+  const int n_items = n_chunks * n_rb;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = resident_ctas(kern);
+  if (per_sm < 1 || nsm < 1) return false;
+  int grid = std::min(nsm * per_sm, n_items);
+  const bool bil = acc == ACC_CODES || acc == ACC_LEFT;
+  if (bil) grid = std::min(grid, nbx);  // one partial row per CTA
+  if (grid < 1) return false;
+  kern<<<grid, 128, 0, s>>>(p, n_chunks, n_items);
+  count_launch();
+  *err = cudaGetLastError();
+  return true;
+}
+
+}  // namespace sten4
+}  // namespace mmc

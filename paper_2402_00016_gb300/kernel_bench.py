@@ -31,6 +31,10 @@ def main(argv=None):
     ap.add_argument("--autotune", action="store_true", help="pick the kernel variant with mmc_autotune first")
     ap.add_argument("--graphs", type=int, default=1, help="replay step chains as CUDA graphs")
     ap.add_argument("--rmax", type=int, default=16, help="largest rhs block of the field layout (8 or 16)")
+    ap.add_argument("--version", type=int, default=0, help="step-kernel version (0: keep the default)")
+    ap.add_argument("--hint", type=int, default=-1, help="store hint of version 4 (1: L2 evict-first)")
+    ap.add_argument("--sweep", default=None,
+                    help="JSON list of variants {version, rpt, minb, spc, blocked, hint}: time each in turn")
     ap.add_argument("--deflate", type=int, default=0,
                     help="k > 0: random deflation space of k vectors, levels deflated (tensor-core projections)")
     a = ap.parse_args(argv)
@@ -50,6 +54,10 @@ def main(argv=None):
             mmc.mmc_set_step_variant(ctx, prec, 0, 200 + a.blocked, 0)
         if a.ns >= 0:
             mmc.mmc_set_step_variant(ctx, prec, 0, 300 + a.ns, 0)
+        if a.version > 0:
+            mmc.mmc_set_step_variant(ctx, prec, 0, 100 + a.version, 0)
+        if a.hint >= 0:
+            mmc.mmc_set_step_variant(ctx, prec, 0, 400 + a.hint, 0)
         tuned = mmc.mmc_autotune(ctx, a.nrhs, prec) if a.autotune else None
         if a.deflate > 0:
             vol12 = 12 * int(np.prod(a.dims))
@@ -64,24 +72,32 @@ def main(argv=None):
         h = mmc.mmc_poly_from_roots(ctx, theta)
         h2 = mmc.mmc_poly_from_roots(ctx, theta[:2]) if a.deflate > 0 else mmc.MMC_ZERO
         defl = 1 if a.deflate > 0 else 0
-        mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, 0, 1, prec)  # warm-up
-        mmc.mmc_profile(ctx, 1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for r in range(a.reps):
-            mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, a.nrhs * (r + 1), 1, prec)
-        e1.record()
-        torch.cuda.synchronize()
-        p = mmc.mmc_profile_read(ctx)
+        variants = json.loads(a.sweep) if a.sweep else [None]
         vol = int(np.prod(a.dims))
-        out = {"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "degree": a.degree,
-               "graphs": a.graphs, "rmax": a.rmax,
-               "step_launches": p["step_launches"], "avg_launch_ms": p["step_ms"] / max(1, p["step_launches"]),
-               "algorithmic_GBps": p["step_bytes"] / p["step_ms"] / 1e6 if p["step_ms"] else 0,
-               "TFLOPs": p["step_flops"] / p["step_ms"] / 1e9 if p["step_ms"] else 0,
-               "ps_per_site_rhs": 1e9 * p["step_ms"] / max(1, p["step_launches"]) / (vol * a.nrhs),
-               "wall_ms": e0.elapsed_time(e1), "variant": tuned}
-        print(json.dumps(out), flush=True)
+        for var in variants:
+            if var is not None:
+                v = {"version": 2, "rpt": 1, "minb": 4, "spc": 64, "blocked": 0, "ns": 0}
+                v.update(var)
+                for rc in (0, 1):
+                    mmc.mmc_set_step_variant_class(ctx, prec, rc, v)
+                mmc.mmc_set_step_variant(ctx, prec, 0, 400 + int(var.get("hint", 0)), 0)
+            mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, 0, 1, prec)  # warm-up
+            mmc.mmc_profile(ctx, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for r in range(a.reps):
+                mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, a.nrhs * (r + 1), 1, prec)
+            e1.record()
+            torch.cuda.synchronize()
+            p = mmc.mmc_profile_read(ctx)
+            out = {"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "degree": a.degree,
+                   "graphs": a.graphs, "rmax": a.rmax,
+                   "step_launches": p["step_launches"], "avg_launch_ms": p["step_ms"] / max(1, p["step_launches"]),
+                   "algorithmic_GBps": p["step_bytes"] / p["step_ms"] / 1e6 if p["step_ms"] else 0,
+                   "TFLOPs": p["step_flops"] / p["step_ms"] / 1e9 if p["step_ms"] else 0,
+                   "ps_per_site_rhs": 1e9 * p["step_ms"] / max(1, p["step_launches"]) / (vol * a.nrhs),
+                   "wall_ms": e0.elapsed_time(e1), "variant": var if var is not None else tuned}
+            print(json.dumps(out), flush=True)
     finally:
         mmc.mmc_destroy(ctx)
 

@@ -120,6 +120,10 @@ _SIGS = {
     "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
     "mmc_leja_order": (_i, [_i, _dp, _dp]),
     "mmc_eig": (_i, [_i, _dp, _i, _dp, _dp]),
+    "mmc_deflation_pairs": (_i, [_i, _dp, _dp, _d, _i, _ip, _ip, _ip]),
+    "mmc_set_deflation_bound": (_i, [_vp, _d]),
+    "mmc_probe_colouring": (_i, [_ip, _i, _ip, _ip]),
+    "mmc_deflation_condition": (_i, [_i, _dp, _i, _ip, _d, _ip, _ip]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -496,3 +500,42 @@ def mmc_eig(A, vectors=False):
         return ev
     V = (vr[0::2] + 1j * vr[1::2]).reshape(n, n, order="F")
     return ev, V
+
+
+def mmc_deflation_pairs(lam, res, tol_accept, k):
+    """(keep, partner): candidate indices of the kept eigenpairs and their gamma_5 partners."""
+    lam, p = _cplx(lam)
+    res = np.ascontiguousarray(res, dtype=np.float64)
+    m = lam.size
+    keep = np.zeros(max(1, m), dtype=np.int32)
+    partner = np.zeros(max(1, m), dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check(lib.mmc_deflation_pairs(int(m), p, res.ctypes.data_as(_dp), float(tol_accept), int(k),
+                                   keep.ctypes.data_as(_ip), partner.ctypes.data_as(_ip), ctypes.byref(n)))
+    return [int(v) for v in keep[: n.value]], [int(v) for v in partner[: n.value]]
+
+
+def mmc_deflation_condition(S, mates, max_u=100.0):
+    """Kept positions of the pairs after the overlap drop rules."""
+    S = np.asfortranarray(S, dtype=np.complex128)
+    q = S.shape[0]
+    mates = np.ascontiguousarray(mates, dtype=np.int32)
+    sel = np.zeros(max(1, q), dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check(lib.mmc_deflation_condition(int(q), S.ctypes.data_as(_dp), int(q), mates.ctypes.data_as(_ip),
+                                       float(max_u), sel.ctypes.data_as(_ip), ctypes.byref(n)))
+    return [int(v) for v in sel[: n.value]]
+
+
+def mmc_set_deflation_bound(ctx, max_u):
+    _check(lib.mmc_set_deflation_bound(ctx, float(max_u)), ctx)
+
+
+def mmc_probe_colouring(dims, reach):
+    """(colour per site, number of colours) of the probing colouring; pure host."""
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    V = int(np.prod(dims))
+    colour = np.zeros(V, dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check(lib.mmc_probe_colouring(d, int(reach), colour.ctypes.data_as(_ip), ctypes.byref(n)))
+    return colour, n.value

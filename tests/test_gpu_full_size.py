@@ -10,10 +10,19 @@ matrix) and the level sample eta_j^H p(M) eta_j (Eq. 2 with the polynomial of
 Sec. 3 given by its roots) for noise indices j spread over several rhs blocks,
 including the first and the last.
 
+The chains the benchmark itself runs (degree 32 - 8 over 512 noises, 128 - 32 over
+128, the 40 x 8 double polynomial of degree 319 - 128 over 32) are checked against
+samples the oracle computed once, stored with the command that wrote them
+(tests/golden/make_c4_levels.py, oracle only).
+
 Tolerances as in the small-lattice tests: FP32 storage 1e-5 relative (normwise for
-M eta; for the bilinear 1e-5 ||eta|| ||p(M) eta||, Cauchy-Schwarz applied to a
+M eta, and element-wise against the largest element, so that one wrong site
+fails; for the bilinear 1e-5 ||eta|| ||p(M) eta||, Cauchy-Schwarz applied to a
 normwise error of p(M) eta), BF16 storage 2^-8 + 1e-6 (Z(4) inputs are exact in
 BF16, one rounding of the output)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -27,8 +36,10 @@ SAMPLED = (0, 5, 300, 511)  # rhs blocks 0, 0, 18, 31 of the 512 batch
 LEVEL = 4
 THETA = np.array([1.0 + 0.8j, 1.0 - 0.8j, 0.3 + 0.0j])  # p of degree 2 (two matvecs)
 
-# (version, rpt, minb) of the forms exercised: v2 lane widths and v3 thread widths
-FORMS = [(2, 1, 4), (2, 2, 3), (3, 1, 1), (3, 2, 1)]
+# (version, rpt, minb, traversal, store hint) of the forms exercised: v2 lane widths, v3 thread
+# widths, v4 register caps, traversals (0 lexicographic, 1 4D blocks, 2 z-halves) and hints
+FORMS = [(2, 1, 4, 0, 0), (2, 2, 3, 0, 0), (3, 1, 1, 0, 0), (3, 2, 1, 0, 0),
+         (4, 1, 4, 0, 0), (4, 1, 3, 2, 1), (4, 1, 4, 1, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -69,10 +80,11 @@ def _column(mmc, field, prec, nrhs, V, j):
 
 
 def _set_form(mmc, ctx, prec, form):
-    ver, rpt, minb = form
-    v = {"version": ver, "rpt": rpt, "minb": minb, "spc": 64, "blocked": 0, "ns": 0}
+    ver, rpt, minb, order, hint = form
+    v = {"version": ver, "rpt": rpt, "minb": minb, "spc": 64, "blocked": order, "ns": 0}
     for rc in (0, 1):
         mmc.mmc_set_step_variant_class(ctx, prec, rc, v)
+    mmc.mmc_set_step_variant(ctx, prec, 0, 400 + hint, 0)
 
 
 def test_column_extraction_matches_unpack(mmc, big):
@@ -101,6 +113,8 @@ def test_apply_M_full_size(mmc, big, prec, form):
             got = _column(mmc, y, prec, nrhs, V, j)
             want = big["M"][j]
             assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol, (nrhs, j)
+            # element-wise: a single wrong element (an indexing error at one site) must fail too
+            assert np.abs(got - want).max() <= tol * np.abs(want).max(), (nrhs, j)
         del x, y
 
 
@@ -113,3 +127,37 @@ def test_level_samples_full_size(mmc, big, form):
     st = mmc.mmc_trace_level(ctx, h, mmc.MMC_ZERO, mmc.MMC_THETA_ONE, 0, 512, 0, LEVEL, mmc.MMC_F32)
     for j in SAMPLED:
         assert abs(st["samples"][j] - big["bil"][j]) < 1e-5 * big["bil_scale"][j], j
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c4_24x24x24x24_levels.json")
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("form", [FORMS[0], FORMS[4], FORMS[5]])
+def test_benchmark_levels_full_size(mmc, big, form):
+    """The level chains the benchmark runs at 24^4, in FP32 storage, against samples the
+    oracle computed once (tests/golden/make_c4_levels.py): p_32 - p_8 over 512 noises,
+    p_128 - p_32 over 128 and p_dbl(40 x 8, degree 319) - p_128 over 32, with the oracle's
+    roots fed to the library.  Bound per sample: 1e-5 of ||eta|| (||p_hi eta|| + ||p_lo eta||)
+    (FP32 storage, Cauchy-Schwarz on a normwise error of the chains' vectors)."""
+    ctx = big["ctx"]
+    gold = _golden()
+    cx = lambda a: np.array([complex(r, i) for r, i in a])
+    _set_form(mmc, ctx, mmc.MMC_F32, form)
+    h = {name: mmc.mmc_poly_from_roots(ctx, cx(gold["roots"][name])) for name in ("p8", "p32", "p128")}
+    h_in = mmc.mmc_poly_from_roots(ctx, cx(gold["roots"]["in"]))
+    h_out = mmc.mmc_poly_from_roots(ctx, cx(gold["roots"]["out"]))
+    h["dbl"] = mmc.mmc_poly_double(ctx, h_in, h_out)
+    assert mmc.mmc_poly_degree(ctx, h["dbl"]) == 319
+    for lv in gold["levels"]:
+        st = mmc.mmc_trace_level(ctx, h[lv["hi"]], h[lv["lo"]], mmc.MMC_THETA_ONE, 0, lv["n_noise"], 0, lv["level"],
+                                 mmc.MMC_F32)
+        for smp in lv["samples"]:
+            want = complex(*smp["sample"])
+            got = st["samples"][smp["j"]]
+            assert abs(got - want) <= 1e-5 * smp["scale"], (lv["level"], smp["j"], got, want, smp["scale"])
