@@ -140,6 +140,25 @@ def pp_arnoldi_eigenpairs(op, gamma5, theta_poly, b, m_arnoldi, k, tol_accept=1e
     return lam[kept], Z, U, res[kept]
 
 
+def deflate_vector(Z, U, b):
+    """b - Z (U^H b): b without its components along the right eigenvectors z_i (U^H Z = I)."""
+    return b - Z @ (U.conj().T @ b)
+
+
+def deflated_double_poly_roots(op, b, m_in, m_out, Z, U):
+    """Deflated double polynomial.  The paper names it (abstract, Sec. 7, Sec. 9: a deflated
+    polynomial lowers the degree of the highest-degree polynomial) without giving its
+    construction.  Reading taken: theta_in from GMRES(m_in) on M from b as in Sec. 5;
+    theta_out from GMRES(m_out) on phi_in(M) = M p_in(M) from the start vector with the
+    deflated eigenvector components removed, b - Z U^H b.  The Krylov space then avoids
+    those components (exactly so for exact eigenvectors), so pi_out spends no roots on
+    phi_in at the deflated eigenvalues, whose part of every level is traced exactly."""
+    theta_in = krylov.gmres_poly_roots(op, b, m_in)
+    phi_in = lambda v: op(krylov.apply_poly(op, theta_in, v))
+    theta_out = krylov.gmres_poly_roots(phi_in, deflate_vector(Z, U, b), m_out)
+    return theta_in, theta_out
+
+
 def biorthonormalise(Z, W):
     """U = W (W^H Z)^{-H}, so that U^H Z = I."""
     S = W.conj().T @ Z

@@ -12,7 +12,7 @@ Contents:
 * M eta_j and p_hi(M) eta_j element statistics for element-wise checks are not
   stored (the vectors are 4M entries); the GPU tests check those at sampled sites.
 
-Run once on a CPU (about 25 minutes on 8 cores):
+Run once on a CPU (about 35 minutes on 8 cores):
     python tests/golden/make_c4_levels.py
 """
 import json

@@ -95,3 +95,61 @@ def test_condition_repeats_until_bounded():
     sel, Inv = deflation.condition_selection(S, [0, 1])
     assert len(sel) == 1
     assert np.allclose(Inv, 1.0 / np.conj(S[sel[0], sel[0]]))
+
+
+def _tiny():
+    import synth
+    from oracle import wilson
+    dims, shape = (2, 2, 2, 4), (4, 2, 2, 2, 4, 3)
+    U = synth.random_gauge(dims, 0.3, 1)
+    op = lambda v: wilson.apply_M(U, 0.155, v.reshape(shape + v.shape[1:])).reshape(v.shape)
+    A = wilson.dense_M(U, 0.155)
+    return dims, op, A
+
+
+def test_deflated_start_vector_keeps_krylov_space_in_complement():
+    """With exact eigenvectors the deflated start vector has no component along them
+    (U^H b' = 0) and neither has any phi_in^j b': the space GMRES builds for p_out."""
+    from oracle import krylov, noise
+    dims, op, A = _tiny()
+    lam, R = np.linalg.eig(A)
+    Lf = np.linalg.inv(R).conj().T  # left eigenvectors, Lf^H R = I
+    idx = np.argsort(np.abs(lam))[:6]
+    Z, U = R[:, idx], Lf[:, idx]
+    b = noise.z4_noise(dims, 1, 0, 0, noise.TAG_GMRES).ravel()
+    bp = deflation.deflate_vector(Z, U, b)
+    assert np.abs(U.conj().T @ bp).max() < 1e-10 * np.linalg.norm(b)
+    # the removed part is exactly the spectral component: b = b' + Z U^H b
+    assert np.allclose(bp + Z @ (U.conj().T @ b), b, atol=1e-12)
+    th_in = krylov.gmres_poly_roots(op, b, 4)
+    v = bp
+    for j in range(5):
+        v = op(krylov.apply_poly(op, th_in, v))
+        assert np.abs(U.conj().T @ v).max() < 1e-9 * np.linalg.norm(v), j
+    t_in, t_out = deflation.deflated_double_poly_roots(op, b, 4, 3, Z, U)
+    assert np.allclose(t_in, th_in)
+    phi = lambda x: op(krylov.apply_poly(op, th_in, x))
+    assert np.allclose(t_out, krylov.gmres_poly_roots(phi, bp, 3))
+
+
+def test_deflated_inverse_level_is_unbiased():
+    """Tr(M^-1 - p_dbl) = E[eta^H (A - sum_i c_i z_i u_i^H) eta] + sum_i c_i u_i^H z_i with
+    c_i = 1/lambda_i - p_dbl(lambda_i), for Z(4) noise (E[eta^H B eta] = Tr B), with the
+    double polynomial built from the deflated start vector; exact with dense matrices."""
+    from oracle import krylov, noise
+    dims, op, A = _tiny()
+    lam, R = np.linalg.eig(A)
+    Lf = np.linalg.inv(R).conj().T
+    idx = np.argsort(np.abs(lam))[:6]
+    Z, U, lz = R[:, idx], Lf[:, idx], lam[idx]
+    b = noise.z4_noise(dims, 1, 0, 0, noise.TAG_GMRES).ravel()
+    t_in, t_out = deflation.deflated_double_poly_roots(op, b, 4, 3, Z, U)
+    n = A.shape[0]
+    P = krylov.apply_double(lambda X: A @ X, t_in, t_out, np.eye(n))
+    Ainv = np.linalg.inv(A)
+    c = 1.0 / lz - krylov.double_scalar(t_in, t_out, lz)
+    B = Ainv - P - (Z * c) @ U.conj().T
+    corr = np.sum(c * np.einsum("ij,ij->j", U.conj(), Z))
+    assert abs(np.trace(B) + corr - np.trace(Ainv - P)) < 1e-9 * abs(np.trace(Ainv))
+    # the deflated operator annihilates the deflated eigenvectors: B z_i = 0
+    assert np.abs(B @ Z).max() < 1e-8 * np.abs(Ainv).max()
