@@ -102,16 +102,46 @@ def level_plan(h):
             (h["p128"], h["p32"], 1, 128, 3), (h["p32"], h["p8"], 1, 512, 4)]
 
 
-# matvecs per sample of the polynomial parts (solves excluded) -- used to scale the CPU legs
-POLY_MATVECS = 8 * 319 + 32 * (319 + 128) + 128 * (128 + 32) + 512 * (32 + 8)
-SAMPLES = 8 + 32 + 128 + 512
+# matvecs per sample of the polynomial parts of each level (the M^-1 level's solves come on top)
+POLY_MATVECS_BY_LEVEL = [319, 319 + 128, 128 + 32, 32 + 8]
+NOISES = [8, 32, 128, 512]
+SAMPLES = sum(NOISES)
 LEVELS = ["M^-1 - p_dbl(40x8)", "p_dbl - p_128", "p_128 - p_32", "p_32 - p_8"]
-# DRAM traffic / algorithmic bytes of the level-chain step kernel, measured by ncu on 24^4 with
-# 64 right-hand sides (6.704 GB of dram__bytes_read+write against 4.544 GB algorithmic)
-TRAFFIC_RATIO = 6.704 / 4.544
+# Matvecs per sample of each level as the library's estimator spends them on this workload
+# (its own counters, mmc_level_stats.matvecs / noises, of an earlier run of this command: the
+# M^-1 level's refined, deflated, polynomial-preconditioned solves included).  The CPU legs
+# charge the oracle the same work per sample, so they time the same algorithm.
+MATVECS_PER_SAMPLE = [28328 / 8, 14304 / 32, 20480 / 128, 20480 / 512]
+# DRAM traffic of the dominant step-kernel class, per site and right-hand side, from one ncu
+# capture per kernel form (dram__bytes_read.sum + dram__bytes_write.sum of a 64-rhs degree-8
+# level chain with the code bilinear at 24^4, the launch scaled to 512 rhs by site-rhs count):
+# keyed by (kernel version, traversal); a form without a capture reports null.
+TRAFFIC_PER_SITE_RHS = {
+    # (kernel version, traversal, class kind, storage precision): bytes per site and rhs
+    (2, 1, "bilinear", 1): (4.671779e9 + 2.024867e9) / (331776 * 64),  # 315.4 B
+    (4, 2, "bilinear", 1): (3.195218e9 + 2.017202e9) / (331776 * 64),  # 245.5 B
+}
 
 
-def oracle_slice(U, kappa, dims, reps):
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_slice(U, kappa, dims, reps, first=0):
     """Time the oracle on a bounded slice: `reps` degree-2 polynomial samples
     eta^H p(M) eta at 24^4 (2 matvecs each).  Returns (seconds, matvecs)."""
     from oracle import krylov, noise, wilson
@@ -120,9 +150,49 @@ def oracle_slice(U, kappa, dims, reps):
     theta = np.array([1.1 + 0.2j, 0.9 - 0.1j, 1.3 + 0.0j])
     t0 = time.time()
     for r in range(reps):
-        eta = noise.z4_noise(dims, 3, r, 4).ravel()
+        eta = noise.z4_noise(dims, 3, first + r, 4).ravel()
         np.vdot(eta, krylov.apply_poly(op, theta, eta))
     return time.time() - t0, 2 * reps
+
+
+def _oracle_worker(args):
+    """One process of the all-core leg: build the gauge field, then time `reps` samples."""
+    reps, first = args
+    import synth
+    W = synth.WORKLOADS[WORKLOAD]
+    U = synth.random_gauge(W.dims, W.eps, W.gauge_seed)
+    return oracle_slice(U, W.kappa, W.dims, reps, first)
+
+
+def cpu_oracle(reps_one, all_cores=True):
+    """The oracle as it stands, on the host cores: one process (numpy single-threaded), then
+    one process per core at once (spawned, one degree-2 sample each).  Seconds per oracle
+    matvec of each leg, the per-level per-noise times they give with the library's matvecs
+    per sample, and samples/s for the workload's noise mix."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"  # every oracle process single-threaded
+    ctx = mp.get_context("spawn")  # never fork a process that holds a CUDA context
+    with ctx.Pool(1) as pool:
+        dt, mv = pool.map(_oracle_worker, [(reps_one, 0)])[0]
+    legs = {"1": {"cores": 1, "s_per_matvec": dt / mv, "sample": "%d degree-2 samples (%d matvecs) in %.1f s"
+                  % (reps_one, mv, dt)}}
+    ncores = os.cpu_count() or 1
+    if all_cores and ncores > 1:
+        t0 = time.time()
+        with ctx.Pool(ncores) as pool:
+            res = pool.map(_oracle_worker, [(1, 100 + i) for i in range(ncores)])
+        wall = time.time() - t0
+        span = max(r[0] for r in res)
+        mvs = sum(r[1] for r in res)
+        legs["all"] = {"cores": ncores, "s_per_matvec": span / mvs,
+                       "sample": "%d processes x 1 degree-2 sample (%d matvecs in all), slowest %.1f s "
+                                 "(%.1f s with gauge generation)" % (ncores, mvs, span, wall)}
+    for leg in legs.values():
+        per_noise = [m * leg["s_per_matvec"] for m in MATVECS_PER_SAMPLE]
+        leg["seconds_per_noise_by_level"] = per_noise
+        leg["value"] = SAMPLES / sum(n * t for n, t in zip(NOISES, per_noise))
+    return legs
 
 
 def run_reference(args, rank):
@@ -134,22 +204,25 @@ def run_reference(args, rank):
     for _ in range(args.warmup):
         oracle_slice(U, W.kappa, W.dims, 1)
     t, mv = 0.0, 0
-    for _ in range(args.steps):
-        dt, m = oracle_slice(U, W.kappa, W.dims, 1)
+    for it in range(args.steps):
+        dt, m = oracle_slice(U, W.kappa, W.dims, 1, first=it)
         t += dt
         mv += m
-    samples = mv / (POLY_MATVECS / SAMPLES)
-    value = samples / t
+    per_noise = [m * t / mv for m in MATVECS_PER_SAMPLE]
+    value = SAMPLES / sum(n * x for n, x in zip(NOISES, per_noise))
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "lattice": "24^4", "eps": W.eps, "kappa": W.kappa,
-                       "levels": LEVELS, "noises": [8, 32, 128, 512], "storage": "f64 (oracle)",
+                       "levels": LEVELS, "noises": NOISES, "storage": "f64 (oracle)",
                        "parallelism": "1 host core"},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "samples/s", "cores": 1,
+                             "cpu": cpu_model(),
+                             "seconds_per_noise_by_level": per_noise,
                              "sample": "per step: one degree-2 polynomial sample (2 oracle matvecs) at 24^4; "
-                                       "samples/s scaled by the workload's %.1f polynomial matvecs per sample "
-                                       "(solves excluded, which favours the oracle)" % (POLY_MATVECS / SAMPLES)},
+                                       "samples/s = the workload's noise mix at the library's matvecs per "
+                                       "sample of each level (solves included) times the oracle's measured "
+                                       "seconds per matvec"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -172,7 +245,9 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
                     help="spinor storage of the polynomial chains (BF16 rounding shifts the level samples by "
                          "several standard errors on this workload: see error_vs_fp64)")
-    ap.add_argument("--cpu-reps", type=int, default=4)
+    ap.add_argument("--cpu-reps", type=int, default=4, help="degree-2 oracle samples of the one-core leg")
+    ap.add_argument("--plain-samples", type=int, default=4,
+                    help="FP64 single-vector samples per level for the plain form")
     ap.add_argument("--tune-file", default=None,
                     help="autotuner cache: load the kernel variants from this JSON file if it exists, else tune "
                          "and write it (a profiling run then reuses the plain run's choices)")
@@ -264,6 +339,7 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     prof = mmc.mmc_profile_read(ctx)
+    classes = mmc.mmc_profile_classes(ctx)
     mmc.mmc_profile(ctx, 0)
     ms_max = ms
     if world > 1:
@@ -294,20 +370,27 @@ def main():
 
     # The plain FP64 single-vector form on the same GPU: same polynomials, deflation and
     # preconditioner, FP64 storage and arithmetic (FP64 solves), one noise vector per call.
-    # Bounded: one sample per level, extrapolated to the 8/32/128/512 mix.
+    # Bounded: args.plain_samples samples per level (fresh noise indices), their mean time
+    # extrapolated to the 8/32/128/512 mix; the spread is reported.
     plain = None
     if rank == 0:
-        per_sample = []
+        per_sample, spread = [], []
         for (hi, lo, defl, n, lvl) in plan:
-            torch.cuda.synchronize()
-            t0 = time.time()
-            mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, 1, 900_000, lvl, mmc.MMC_F64, pre,
-                                want_samples=False)
-            torch.cuda.synchronize()
-            per_sample.append(time.time() - t0)
+            ts = []
+            for q in range(args.plain_samples):
+                torch.cuda.synchronize()
+                t0 = time.time()
+                mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, 1, 900_000 + q, lvl, mmc.MMC_F64, pre,
+                                    want_samples=False)
+                torch.cuda.synchronize()
+                ts.append(time.time() - t0)
+            per_sample.append(float(np.mean(ts)))
+            spread.append([float(np.min(ts)), float(np.max(ts))])
         t_step = sum(n * t for (_, _, _, n, _), t in zip(plan, per_sample))
         plain = {"value": SAMPLES / t_step, "unit": "samples/s", "seconds_per_sample_by_level": per_sample,
-                 "sample": "one FP64 single-vector sample per level, extrapolated to the 8/32/128/512 mix",
+                 "min_max_seconds_by_level": spread,
+                 "sample": "%d FP64 single-vector samples per level (host wall time each), their mean "
+                           "extrapolated to the 8/32/128/512 mix" % args.plain_samples,
                  "speedup_of_value": value / (SAMPLES / t_step)}
 
     # Error of the reduced-precision form against the FP64 form (which the parity tests pin
@@ -327,18 +410,33 @@ def main():
                                 "mean_diff_over_stderr": float(d.real.mean() / se) if se == se else None,
                                 "correction_diff": a["corr_re"] - b["corr_re"]})
 
-    # CPU baseline: the oracle on a bounded slice of the same workload (rank 0 only)
+    # CPU baseline: the oracle on bounded slices of the same workload (rank 0 only), on one
+    # host core and on all of them
     cpu = None
     if rank == 0 and world == 1:
-        dt, mv = oracle_slice(U, W.kappa, W.dims, args.cpu_reps)
-        cpu = {"value": (mv / (POLY_MATVECS / SAMPLES)) / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
-               "sample": "%d degree-2 polynomial samples (%d oracle matvecs, %.1f s) at 24^4, scaled by the "
-                         "workload's %.1f polynomial matvecs per sample (solves excluded, which favours the "
-                         "oracle)" % (args.cpu_reps, mv, dt, POLY_MATVECS / SAMPLES)}
+        legs = cpu_oracle(args.cpu_reps, all_cores=True)
+        best = legs.get("all", legs["1"])
+        cpu = {"value": best["value"], "unit": "samples/s", "cores": best["cores"], "kind": "oracle",
+               "cpu": cpu_model(), "legs": legs,
+               "sample": "oracle seconds per matvec at 24^4 from degree-2 polynomial samples (%s); samples/s = "
+                         "the 8/32/128/512 noise mix at the library's matvecs per sample of each level, the "
+                         "M^-1 level's solves included" % best["sample"]}
 
+    # Roofline of the dominant step-kernel class (the launch class with the most device time in
+    # the timed steps): its algorithmic bytes (mmc_profile_classes: every operand element once,
+    # links once per launch, nothing for the noise codes) over its CUDA-event time.
     peak, peak_kind = measured_peaks()
-    avg_bytes = prof["step_bytes"] / max(1, prof["step_launches"])
-    achieved = prof["step_bytes"] / (prof["step_ms"] / 1e3) / 1e9 if prof["step_ms"] > 0 else 0.0
+    dom = max(classes, key=lambda c: c["ms"]) if classes else None
+    if dom and dom["ms"] > 0:
+        achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+        units = float(np.prod(W.dims)) * dom["nrhs_padded"]  # site-rhs per launch
+        rc = 1 if dom["nrhs_padded"] >= 16 else 0
+        tkey = "%s_%s" % (("f64", "f32", "bf16")[dom["prec"]], "512rhs" if rc else "8rhs")
+        form = tune.get(tkey, {}) if isinstance(tune, dict) else {}
+        tps = TRAFFIC_PER_SITE_RHS.get((form.get("version"), form.get("blocked"), dom["kind"], dom["prec"]))
+        traffic = tps * units if tps else None
+    else:
+        achieved, traffic, units, form = 0.0, None, 0, {}
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -351,16 +449,27 @@ def main():
                               else "p_dbl (degree 319)", "tol": 1e-10, "inner_storage": args.solve_storage}, "l2": "inputs larger than L2 (GB-sized fields)",
                    "parallelism": "replicas" if world > 1 else "1 gpu"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": avg_bytes * TRAFFIC_RATIO,
-                     "traffic_basis": "DRAM bytes per average step launch: its algorithmic bytes x %.3f, the "
-                                      "dram__bytes_read+write / algorithmic ratio of one ncu capture of the "
-                                      "level-chain step kernel (FP32, 16-rhs blocks, 24^4, 64 rhs; "
-                                      "profiles/step2_kernel_f32_codes_24x24x24x24_64rhs.md)" % TRAFFIC_RATIO,
-                     "kernel": "step_kernel (fused stencil + Leja step)",
-                     "peak_kind": peak_kind, "launches": prof["step_launches"],
-                     "avg_launch_ms": prof["step_ms"] / max(1, prof["step_launches"]),
-                     "share_of_step": prof["step_ms"] / ms if ms > 0 else None,
-                     "tflops": prof["step_flops"] / (prof["step_ms"] / 1e3) / 1e12 if prof["step_ms"] else 0},
+                     "frac": achieved / peak,
+                     "traffic": traffic,
+                     "traffic_basis": ("DRAM bytes read and written per launch of this class's kernel form, "
+                                       "from one ncu capture of the same form on a 64-rhs case, scaled by "
+                                       "site-rhs to this launch" if traffic else
+                                       "no DRAM counters were taken for this kernel form"),
+                     "kernel": "step kernel (fused Wilson stencil + Leja step + epilogue), class %s, %s storage, "
+                               "%d rhs per launch" % (dom["kind"], ("f64", "f32", "bf16")[dom["prec"]],
+                                                      dom["nrhs_padded"]) if dom else None,
+                     "form": form,
+                     "algorithmic_bytes_per_launch": dom["bytes"] / max(1, dom["launches"]) if dom else None,
+                     "site_rhs_per_launch": units,
+                     "peak_kind": peak_kind, "launches": dom["launches"] if dom else 0,
+                     "avg_launch_ms": dom["ms"] / max(1, dom["launches"]) if dom else None,
+                     "share_of_step": dom["ms"] / ms if (dom and ms > 0) else None,
+                     "tflops": dom["flops"] / (dom["ms"] / 1e3) / 1e12 if (dom and dom["ms"]) else 0,
+                     "all_step_launches": {"launches": prof["step_launches"], "ms": prof["step_ms"],
+                                           "achieved_GBps": prof["step_bytes"] / (prof["step_ms"] / 1e3) / 1e9
+                                           if prof["step_ms"] else 0.0,
+                                           "share_of_step": prof["step_ms"] / ms if ms > 0 else None},
+                     "classes": classes},
         "gpu_launches": prof["all_launches"],
         "graphs": {"chain_graph_replays": prof["graph_launches"], "note": mmc.mmc_graph_note(ctx)},
         "launch_index_timed_start": launches_before,

@@ -160,6 +160,16 @@ int mmc_noise_noalloc(mmc_ctx* ctx, uint32_t level, uint32_t first, uint32_t tag
  * (MMC_OP_M: p of degree m-1 in M; else p_out in phi_h(M)). */
 int mmc_gmres_poly(mmc_ctx* ctx, int m, int op_handle, double* theta_out, int* handle);
 
+/* The GMRES(m) cycle of mmc_gmres_poly from the start vector with its components
+ * along the context's deflation eigenvectors removed, b <- b - Z (U^H b)
+ * (mmc_deflate or mmc_set_deflation first; MMC_ERR_STATE without eigenpairs).
+ * Reading of the paper's deflated double polynomial (abstract, Sec. 7, Sec. 9:
+ * named, mechanism not given): with op_handle = p_in, the outer polynomial need
+ * not place roots near phi_in at the deflated eigenvalues, which the levels
+ * treat exactly (mmc_trace_level with deflate = 1, also for hi = MMC_INV), so
+ * the same outer degree serves the rest of the spectrum. */
+int mmc_gmres_poly_deflated(mmc_ctx* ctx, int m, int op_handle, double* theta_out, int* handle);
+
 /* Register a polynomial given by m Leja-ordered roots theta (2m doubles), p of
  * degree m-1 with pi(a) = prod (1 - a/theta_i) = 1 - a p(a) (Sec. 3). */
 int mmc_poly_from_roots(mmc_ctx* ctx, int m, const double* theta, int* handle);
@@ -236,9 +246,11 @@ int mmc_solve(mmc_ctx* ctx, const void* b, void* x, int nrhs, double rel_tol, in
 /* One Monte Carlo level (Eq. 2, Sec. 6): n_noise Z(4) vectors (noise indices
  * first_noise.., level id `level`), samples eta^H Theta (A_hi - A_lo) eta with
  * hi in {MMC_INV, polynomial handle}, lo in {polynomial handle, MMC_ZERO}.
- * deflate != 0 (both polynomial) subtracts sum_i c_i (eta^H Theta z_i)(u_i^H eta)
- * with c_i = p_hi(lambda_i) - p_lo(lambda_i) and reports the exact correction
- * (Sec. 7).  prec: storage of the polynomial chains.  For hi = MMC_INV the
+ * deflate != 0 (polynomial operands, or hi = MMC_INV) subtracts
+ * sum_i c_i (eta^H Theta z_i)(u_i^H eta) with c_i = p_hi(lambda_i) - p_lo(lambda_i)
+ * (1/lambda_i in place of p_hi for MMC_INV) and reports the exact correction
+ * (Sec. 7; for MMC_INV the deflated top level that goes with a deflated double
+ * polynomial, see mmc_gmres_poly_deflated).  prec: storage of the polynomial chains.  For hi = MMC_INV the
  * solves use rel_tol 1e-10, preconditioner `precond` and FGMRES(m) with m from
  * mmc_set_solve_params (default 48), with an
  * FP32 inner solve, or FP64 throughout when prec = MMC_F64.
@@ -348,11 +360,28 @@ typedef struct {
   long long graph_captures; /* of which captured (and instantiated) first */
 } mmc_profile_stats;
 
+/* The same counters per launch class: the step chains of one kind (with a
+ * bilinear epilogue, accumulating into a field, with an aux operand such as the
+ * Horner chains of the solves' preconditioner, or plain M) at one precision and
+ * padded rhs count.  The time of a chain replayed from its CUDA graph is that
+ * of the whole replay; launches, bytes and flops count its steps. */
+enum { MMC_PROF_PLAIN = 0, MMC_PROF_BILINEAR = 1, MMC_PROF_ACCUMULATE = 2, MMC_PROF_AUX = 3 };
+typedef struct {
+  int kind;          /* MMC_PROF_* */
+  int prec;          /* storage precision of the chain */
+  int nrhs_padded;   /* right-hand sides per launch, padded to the rhs block */
+  long long launches;
+  double ms, bytes, flops;
+} mmc_profile_class;
+
 /* enable != 0 starts recording (counters reset); 0 stops.  While enabled every
  * step launch is bracketed by CUDA events on its stream. */
 int mmc_profile(mmc_ctx* ctx, int enable);
 /* Synchronise the context's work and read the counters. */
 int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out);
+/* Synchronise and copy up to max_classes per-class counters (in order of first
+ * use since profiling was enabled) to out; *n_classes receives how many exist. */
+int mmc_profile_classes(mmc_ctx* ctx, int max_classes, mmc_profile_class* out, int* n_classes);
 
 /* Inner FGMRES length and outer-cycle limit of the solves inside mmc_trace_level
  * (Sec. 1 and Sec. 8: the solves of the M^-1 level; defaults 48 and 400).
@@ -379,7 +408,11 @@ int mmc_set_rhs_block_max(mmc_ctx* ctx, int rmax);
  * wait_iters polls (0: the kernel's default, well over a second).  The kernel
  * then raises its error flag and returns, and the next synchronising call
  * (a level, a solve, a reduction) returns MMC_ERR_TIMEOUT with the context
- * still usable.  enable = 0 restores normal operation. */
+ * still usable.  enable = 0 restores normal operation.  (Should the producer's
+ * own bounded wait for its copies in flight ever give up, a copy might land
+ * after its CTA exited: that call also returns MMC_ERR_TIMEOUT, and the context
+ * is retired, every later call on it returning MMC_ERR_STATE until it is
+ * destroyed.) */
 int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters);
 
 /* Not part of the paper (launch tuning of the a1/a5 step kernel, Sec. 1 and
@@ -394,11 +427,14 @@ int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters);
  * warp, for Lx * R up to 384, falling back to 2 otherwise; 4: as 2 with one
  * rhs per lane, a persistent grid whose CTAs take (rhs block, pass of sites)
  * items round-robin so that the sites in flight form one compact front, and
- * the loads of each hop issued while the previous hop computes), or 200 + b
+ * the loads of each hop issued while the previous hop computes; 5: as 4 with
+ * the operands of the hops staged in shared memory by per-lane asynchronous
+ * copies several hops ahead, the depth set by 300 + n, FP32 3 or 4 (default 4),
+ * BF16 4 (default) or 6), or 200 + b
  * for the site traversal of versions 2 and 4 (b = 0 lexicographic, 1 4 x 4 x 2
  * x 2 blocks when the extents are divisible, 2 z-half by z-half with t outermost
  * within a half when Lz is even), or 300 + n to give version 3 n ring slots
- * (2..6; 300: as many as fit), or 400 + h for the store hint of version 4 (h =
+ * (2..6; 300: as many as fit) and version 5 its pipeline depth, or 400 + h for the store hint of version 4 (h =
  * 1: results stored with an L2 evict-first policy, 0: default); spc = sites per
  * CTA (16..1024, power of two).  Values <= 0 keep the current setting.  Version 3 bounds every
  * wait for its staged rows; a wait that gives up makes the next call that
@@ -406,9 +442,10 @@ int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters);
 int mmc_set_step_variant(mmc_ctx* ctx, int prec, int rpt, int minb, int spc);
 /* The whole variant of one rhs-block class at once: rhs_class 0 for batches
  * whose block R is below 16 (up to 8 vectors, e.g. the solves of the M^-1
- * level), 1 for R = 16; version 1..4 (F64: 1), rpt 1 or 2, minb 1..8, spc as
- * above, blocked = traversal 0..2, ns 0 or 2..6.  MMC_ERR_ARG on any value out
- * of range.  The store hint of version 4 is set by mmc_set_step_variant. */
+ * level), 1 for R = 16; version 1..5 (F64: 1), rpt 1 or 2, minb 1..8, spc as
+ * above, blocked = traversal 0..2, ns 0 or 2..6 (version 5: its depth, 0 for
+ * 4).  MMC_ERR_ARG on any value out of range.  The store hint of version 4 is
+ * set by mmc_set_step_variant. */
 int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int version, int rpt, int minb, int spc,
                                int blocked, int ns);
 /* Step chains (the degrees of a polynomial applied to a batch, Sec. 3, Sec. 5) run

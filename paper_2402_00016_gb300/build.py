@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmmc.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["stencil.cu", "stencil2_f32.cu", "stencil2_bf16.cu", "stencil3_f32.cu", "stencil4_f32.cu", "stencil4_bf16.cu", "blas.cu", "api.cu", "levels.cu", "noalloc.cu", "net.cu", "tc_proj.cu", "learned.cu", "estimate.cu", "dense.cpp", "deflation_select.cpp"]
+SOURCES = ["stencil.cu", "stencil2_f32.cu", "stencil2_bf16.cu", "stencil3_f32.cu", "stencil4_f32.cu", "stencil4_bf16.cu", "stencil5_f32.cu", "stencil5_bf16.cu", "blas.cu", "api.cu", "levels.cu", "noalloc.cu", "net.cu", "tc_proj.cu", "learned.cu", "estimate.cu", "dense.cpp", "deflation_select.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -207,6 +207,7 @@ int mmc_profile(mmc_ctx* ctx, int enable) {
   if (enable) {
     ctx->prof_launches = 0;
     ctx->prof_ms = ctx->prof_bytes = ctx->prof_flops = 0;
+    ctx->prof_classes.clear();
     ctx->launches0 = mmc::launch_count();
     ctx->graph_launches0 = ctx->graph_launches;
     ctx->graph_captures0 = ctx->graph_captures;
@@ -227,6 +228,16 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out) {
   out->all_launches = mmc::launch_count() - ctx->launches0;
   out->graph_launches = ctx->graph_launches - ctx->graph_launches0;
   out->graph_captures = ctx->graph_captures - ctx->graph_captures0;
+  return MMC_OK;
+}
+
+int mmc_profile_classes(mmc_ctx* ctx, int max_classes, mmc_profile_class* out, int* n_classes) {
+  if (!ctx || !n_classes || max_classes < 0 || (max_classes > 0 && !out)) return MMC_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(prof_collect(ctx));
+  *n_classes = int(ctx->prof_classes.size());
+  for (int i = 0; i < std::min(max_classes, *n_classes); ++i) out[i] = ctx->prof_classes[i];
   return MMC_OK;
 }
 
@@ -308,12 +319,14 @@ const char* mmc_graph_note(const mmc_ctx* ctx) { return ctx ? ctx->graph_note.c_
 int mmc_set_step_variant_class(mmc_ctx* ctx, int prec, int rhs_class, int version, int rpt, int minb, int spc,
                                int blocked, int ns) {
   if (!ctx || prec < 0 || prec > 2 || rhs_class < 0 || rhs_class > 1) return MMC_ERR_ARG;
-  if (version < 1 || version > 4 || (prec == MMC_F64 && version != 1)) RET(MMC_ERR_ARG, "bad kernel version");
+  if (version < 1 || version > 5 || (prec == MMC_F64 && version != 1)) RET(MMC_ERR_ARG, "bad kernel version");
   if (blocked < 0 || blocked > 2) RET(MMC_ERR_ARG, "traversal must be 0, 1 or 2");
   if (rpt != 1 && rpt != 2) RET(MMC_ERR_ARG, "rpt must be 1 or 2");
   if (minb < 1 || minb > 8) RET(MMC_ERR_ARG, "minb must be 1..8");
   if (spc < 16 || spc > 1024 || (spc & (spc - 1))) RET(MMC_ERR_ARG, "spc must be a power of two in 16..1024");
   if (ns != 0 && (ns < 2 || ns > 6)) RET(MMC_ERR_ARG, "ring slots must be 2..6 (or 0)");
+  if (version == 5 && ns != 0 && ns != (prec == MMC_F32 ? 3 : 6) && ns != 4)
+    RET(MMC_ERR_ARG, "pipeline depth of version 5: 3 or 4 (FP32), 4 or 6 (BF16), 0 for 4");
   ctx->var_ver[prec][rhs_class] = version;
   ctx->var_rpt[prec][rhs_class] = prec == MMC_F64 ? 1 : rpt;
   ctx->var_minb[prec][rhs_class] = minb;
@@ -332,7 +345,8 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
   TRY(scratch(ctx, "tune_x", field_bytes(g, prec), &x));
   TRY(scratch(ctx, "tune_y", field_bytes(g, prec), &y));
   TRY(scratch(ctx, "tune_codes", size_t(g.npad) * g.V * sizeof(uint32_t), &codes));
-  const int nbx = nbx_step(ctx);
+  // one row of bilinear partials per CTA of every variant tried, down to 16 sites per CTA
+  const int nbx = std::max(nbx_step(ctx), nbx_for(ctx, 16));
   TRY(scratch(ctx, "tune_part", size_t(nbx) * g.npad * sizeof(double2), &part));
   std::vector<uint2> ids(g.npad);
   for (int r = 0; r < g.npad; ++r) ids[r] = make_uint2(7u, uint32_t(r));
@@ -436,6 +450,24 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
         bn = nss[ni];
         br = rpts[ri];
         bo = 0;
+      }
+    }
+    // the persistent form with operands staged by asynchronous copies (version 5): depths, traversals
+    for (int ordr = 0; ordr <= 2; ++ordr)
+    for (int dp = 0; dp < 2; ++dp) {
+      if ((ordr == 1 && !ctx->order) || (ordr == 2 && !ctx->order_zh)) continue;
+      const int depth = prec == MMC_F32 ? (dp ? 4 : 3) : (dp ? 6 : 4);
+      ctx->var_ver[prec][rc] = 5;
+      ctx->var_rpt[prec][rc] = 1;
+      ctx->var_ns[prec][rc] = depth;
+      ctx->order_v[prec][rc] = ordr;
+      TRY(time_variant());
+      if (med < best_ms) {
+        best_ms = med;
+        bv = 5;
+        br = 1;
+        bn = depth;
+        bo = ordr;
       }
     }
     // the persistent, pipelined form (version 4, one rhs per lane): register caps and traversals

@@ -88,6 +88,7 @@ struct mmc_ctx {
   long long graph_launches0 = 0;      // value at the last mmc_profile(ctx, 1)
   long long graph_captures = 0, graph_captures0 = 0;
   std::string graph_note;             // why graphs were switched off, if they were
+  bool failed = false;         // set when a kernel may have left work in flight: every later call refuses
   double defl_max_u = 100.0;  // mmc_deflate: bound on the norm of a left vector u_i (a column of (W^H Z)^{-H})
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
@@ -113,7 +114,12 @@ struct mmc_ctx {
   // profiling (mmc_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  struct PendingEv {
+    cudaEvent_t e0, e1;
+    int cls;  // index into prof_classes
+  };
+  std::vector<PendingEv> ev_pending;
+  std::vector<mmc_profile_class> prof_classes;  // per launch class (chain kind, precision, padded rhs)
   long long prof_launches = 0;
   double prof_ms = 0, prof_bytes = 0, prof_flops = 0;
   long long launches0 = 0;
@@ -245,12 +251,13 @@ inline int prof_event(mmc_ctx* ctx, cudaEvent_t* e) {
 // Collect the elapsed times of finished event pairs (synchronises on each pair).
 inline int prof_collect(mmc_ctx* ctx) {
   for (auto& pr : ctx->ev_pending) {
-    CK(cudaEventSynchronize(pr.second));
+    CK(cudaEventSynchronize(pr.e1));
     float ms = 0;
-    CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    CK(cudaEventElapsedTime(&ms, pr.e0, pr.e1));
     ctx->prof_ms += ms;
-    ctx->ev_pool.push_back(pr.first);
-    ctx->ev_pool.push_back(pr.second);
+    if (pr.cls >= 0 && pr.cls < int(ctx->prof_classes.size())) ctx->prof_classes[pr.cls].ms += ms;
+    ctx->ev_pool.push_back(pr.e0);
+    ctx->ev_pool.push_back(pr.e1);
   }
   ctx->ev_pending.clear();
   return MMC_OK;
@@ -301,6 +308,37 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
   const int rpt = rpt_for(ctx, run.prec, g.R);
   const int rc = rclass(g.R);
   const bool prof = ctx->prof;
+  {
+    // The site-chunked forms write one row of bilinear partials per CTA: refuse a launch
+    // whose grid would need more rows than the run's partial buffer holds.
+    int any = 0;
+    for (const Step& st : run.steps) any |= st.flags;
+    if ((any & (mmc::SF_BIL_CODES | mmc::SF_BIL_LEFT)) &&
+        (!run.partial || nbx_for(ctx, ctx->spc_v[run.prec][rc]) > run.nbx))
+      RET(MMC_ERR_ARG, "step chain: bilinear partial buffer has fewer rows than the launch has CTAs");
+  }
+  int cls = -1;  // profiling class of this run: chain kind, precision, padded rhs count
+  if (prof) {
+    int any = 0;
+    for (const Step& st : run.steps) any |= st.flags;
+    const int kind = (any & (mmc::SF_BIL_CODES | mmc::SF_BIL_LEFT)) ? MMC_PROF_BILINEAR
+                     : (any & mmc::SF_YACC)                          ? MMC_PROF_ACCUMULATE
+                     : (any & mmc::SF_AUX)                           ? MMC_PROF_AUX
+                                                                     : MMC_PROF_PLAIN;
+    for (size_t c = 0; c < ctx->prof_classes.size(); ++c) {
+      const mmc_profile_class& pc = ctx->prof_classes[c];
+      if (pc.kind == kind && pc.prec == run.prec && pc.nrhs_padded == g.npad) cls = int(c);
+    }
+    if (cls < 0) {
+      mmc_profile_class pc;
+      std::memset(&pc, 0, sizeof(pc));
+      pc.kind = kind;
+      pc.prec = run.prec;
+      pc.nrhs_padded = g.npad;
+      ctx->prof_classes.push_back(pc);
+      cls = int(ctx->prof_classes.size()) - 1;
+    }
+  }
   // one launch per step; with per-launch profiling events unless the chain is captured
   auto launch_steps = [&](bool events, cudaStream_t s) -> int {
     for (size_t k = 0; k < run.steps.size(); ++k) {
@@ -343,7 +381,15 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
         CK(cudaEventRecord(e0, s));
       }
       bool done = false;
-      if (ctx->var_ver[run.prec][rc] == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      if (ctx->var_ver[run.prec][rc] == 5 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+        cudaError_t e5 = cudaSuccess;
+        const int ns = ctx->var_ns[run.prec][rc];
+        const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
+        done = run.prec == MMC_F32 ? mmc::launch_step5_f32(g.R, ns == 3 ? 3 : 4, p, g.nrb, nbx, s, &e5)
+                                   : mmc::launch_step5_bf16(g.R, ns == 6 ? 6 : 4, p, g.nrb, nbx, s, &e5);
+        CK(e5);
+      }
+      if (!done && ctx->var_ver[run.prec][rc] == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e4 = cudaSuccess;
         const int mb = ctx->var_minb[run.prec][rc] == 3 ? 3 : 4;
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
@@ -366,7 +412,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec][rc], p, g.nrb, s));
       if (events) {
         CK(cudaEventRecord(e1, s));
-        ctx->ev_pending.push_back({e0, e1});
+        ctx->ev_pending.push_back({e0, e1, cls});
         if (ctx->ev_pending.size() > 65536) TRY(prof_collect(ctx));
       }
     }
@@ -451,7 +497,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     ctx->graph_launches += 1;
     if (prof) {
       CK(cudaEventRecord(e1, s));
-      ctx->ev_pending.push_back({e0, e1});
+      ctx->ev_pending.push_back({e0, e1, cls});
       if (ctx->ev_pending.size() > 65536) TRY(prof_collect(ctx));
     }
   }
@@ -472,8 +518,14 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
                              ((st.flags & mmc::SF_YACC) ? 2.0 * 12 * (run.prec == MMC_F64 ? 16 : 8) : 0.0) +
                              ((st.flags & mmc::SF_BIL_LEFT) ? sb : 0.0);
       const double links = (st.flags & mmc::SF_HOP) ? 4.0 * 9 * (run.prec == MMC_F64 ? 16 : 8) : 0.0;
-      ctx->prof_bytes += double(ctx->V) * (double(g.npad) * per_rhs + links);
-      ctx->prof_flops += double(ctx->V) * g.npad * (((st.flags & mmc::SF_HOP) ? 1368.0 : 0.0) + 48.0);
+      const double bytes = double(ctx->V) * (double(g.npad) * per_rhs + links);
+      const double flops = double(ctx->V) * g.npad * (((st.flags & mmc::SF_HOP) ? 1368.0 : 0.0) + 48.0);
+      ctx->prof_bytes += bytes;
+      ctx->prof_flops += flops;
+      mmc_profile_class& pc = ctx->prof_classes[cls];
+      pc.launches += 1;
+      pc.bytes += bytes;
+      pc.flops += flops;
     }
     if (st.flags & mmc::SF_HOP) ctx->matvecs += g.npad;
   }
@@ -486,6 +538,13 @@ inline int check_step_err(mmc_ctx* ctx, cudaStream_t s) {
   int h = 0;
   CK(cudaMemcpyAsync(&h, ctx->step_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (h == 2) {
+    // a staged copy may have been in flight when its CTA exited: nothing launched on this
+    // context can be trusted any more
+    ctx->failed = true;
+    RET(MMC_ERR_TIMEOUT, "step kernel: a bounded wait for staged copies gave up with copies in flight; "
+                         "the context is retired (destroy it)");
+  }
   if (h) {
     CK(cudaMemsetAsync(ctx->step_err, 0, sizeof(int), s));
     RET(MMC_ERR_TIMEOUT, "step kernel: a bounded wait for staged rows gave up");
@@ -797,6 +856,7 @@ int net_apply(mmc_ctx* ctx, int h, const void* x, void* y, int nrhs, cudaStream_
 
 inline int check_ctx(mmc_ctx* ctx) {
   if (!ctx) return MMC_ERR_ARG;
+  if (ctx->failed) RET(MMC_ERR_STATE, "context retired after a failed kernel (destroy it)");
   if (!ctx->gauge) RET(MMC_ERR_STATE, "no gauge field loaded");
   CK(cudaSetDevice(ctx->device));
   return MMC_OK;

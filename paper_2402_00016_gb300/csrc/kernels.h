@@ -31,6 +31,12 @@ bool launch_step2_bf16(int R, int rpt, int minb, const step_params& p, int n_rb,
 // bilinear partials.  Returns false when the flags need another form.
 bool launch_step4_f32(int R, int minb, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err);
 bool launch_step4_bf16(int R, int minb, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err);
+// Fifth form (stencil5.cuh): as the fourth, with the hops' operands staged in shared
+// memory by per-lane asynchronous copies `depth` stages ahead (FP32: 3 or 4, BF16: 4
+// or 6); one rhs per lane, R = 8 or 16, 128 registers.  Returns false when the flags
+// or the operands' alignment need another form.
+bool launch_step5_f32(int R, int depth, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err);
+bool launch_step5_bf16(int R, int depth, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err);
 // Staged form (rows by bulk asynchronous copies, stencil3.cuh) for FP32 (prec 1) and BF16
 // (prec 2) storage, R = 8 or 16, rpt = 1 or 2 rhs per thread; nbx: rows of the bilinear
 // partials (grid bound), ns: ring slots (0: as many as fit).  Returns false when the

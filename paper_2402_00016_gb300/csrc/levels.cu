@@ -564,6 +564,9 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     RET(MMC_ERR_ARG, "mmc_trace_level: bad level operands");
   if (deflate && (is_net(ctx, hi) || is_net(ctx, lo)))
     RET(MMC_ERR_ARG, "mmc_trace_level: deflation needs polynomial operands (c_i = p_hi(lambda_i) - p_lo(lambda_i))");
+  if (deflate && hi == MMC_INV && ctx->k_defl > 0)
+    for (const cd& l : ctx->lambda)
+      if (l == cd(0, 0)) RET(MMC_ERR_ARG, "mmc_trace_level: a deflated eigenvalue is zero (c_i = 1/lambda_i - ...)");
   const auto t0 = std::chrono::steady_clock::now();
   const long long mv0 = ctx->matvecs;
   cudaStream_t s = ctx->stream;
@@ -672,7 +675,7 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
   if (lo != MMC_ZERO && hi != MMC_INV) TRY(poly_bilinear(lo, -1.0));
   cd corr(0, 0);
   int kd = 0;
-  if (deflate && hi != MMC_INV && ctx->k_defl > 0) {
+  if (deflate && ctx->k_defl > 0) {
     const int k = ctx->k_defl;
     kd = k;
     const geom g1 = make_geom(ctx, 1);
@@ -745,7 +748,9 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
       }
     }
     for (int i = 0; i < k; ++i) {
-      cd c = poly_value(ctx, hi, ctx->lambda[i]) - (lo == MMC_ZERO ? cd(0, 0) : poly_value(ctx, lo, ctx->lambda[i]));
+      // c_i: the level's scalar function at lambda_i (1/lambda_i for M^-1)
+      const cd fhi = hi == MMC_INV ? 1.0 / ctx->lambda[i] : poly_value(ctx, hi, ctx->lambda[i]);
+      cd c = fhi - (lo == MMC_ZERO ? cd(0, 0) : poly_value(ctx, lo, ctx->lambda[i]));
       for (int r = 0; r < n_noise; ++r) x[r] -= c * A[size_t(i) * g.npad + r] * B[size_t(i) * g.npad + r];
       corr += c * D[i];
     }
@@ -785,6 +790,58 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     }
   for (int r = 0; r < n_noise; ++r)
     if (!std::isfinite(x[r].real()) || !std::isfinite(x[r].imag())) RET(MMC_ERR_NAN, "mmc_trace_level: NaN sample");
+  return MMC_OK;
+}
+
+int mmc_gmres_poly_deflated(mmc_ctx* ctx, int m, int op_handle, double* theta_out, int* handle) {
+  TRY(check_ctx(ctx));
+  if (m < 1 || !handle) RET(MMC_ERR_ARG, "mmc_gmres_poly_deflated: bad argument");
+  if (ctx->k_defl < 1) RET(MMC_ERR_STATE, "mmc_gmres_poly_deflated: no deflation eigenpairs (mmc_deflate first)");
+  if (op_handle != MMC_OP_M &&
+      (!valid_poly(ctx, op_handle) || ctx->polys[op_handle].kind != 0 || ctx->polys[op_handle].op != MMC_OP_M))
+    RET(MMC_ERR_ARG, "mmc_gmres_poly_deflated: op_handle must be a single polynomial in M");
+  cudaStream_t s = ctx->stream;
+  const geom g = make_geom(ctx, 1);
+  void* V;
+  TRY(scratch(ctx, "gmres_V", field_bytes(g, MMC_F64) * (m + 1), &V));
+  std::vector<uint2> ids(g.npad, make_uint2(0u, 0u));
+  void* dids;
+  TRY(scratch(ctx, "ids", ids.size() * sizeof(uint2), &dids));
+  CK(cudaMemcpyAsync(dids, ids.data(), ids.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+  CK(mmc::launch_noise(MMC_F64, g, (const uint2*)dids, MMC_TAG_GMRES, ctx->seed, V, nullptr, s));
+  // b <- b - Z (U^H b): the start vector without its components along the deflated eigenvectors
+  const int k = ctx->k_defl;
+  const int nbx = (g.V + kSpc - 1) / kSpc;
+  void* part;
+  TRY(scratch(ctx, "gd_part", size_t(nbx) * k * g.npad * sizeof(double2), &part));
+  CK(mmc::launch_vec_proj(MMC_F64, g, ctx->U, k, V, kSpc, (double2*)part, s));
+  std::vector<cd> c;
+  TRY(reduce_to_host(ctx, (double2*)part, nbx, k, g.npad, c, s));
+  for (auto& v : c) v = -v;
+  void* dc;
+  TRY(upload(ctx, "gd_coef", c, &dc, s));
+  CK(mmc::launch_vec_update(MMC_F64, g, ctx->Z, k, (const double2*)dc, V, s));
+  ArnoldiOut ao;
+  auto op = [&](const void* in, void* out) { return apply_op_f64(ctx, op_handle, in, out, 1, s); };
+  TRY(arnoldi_cgs2(ctx, g, MMC_F64, V, m, op, ao, s));
+  for (int j = 0; j < m; ++j)
+    if (ao.H[0](j + 1, j) == cd(0, 0) && j < m - 1) RET(MMC_ERR_BREAKDOWN, "Arnoldi breakdown");
+  std::vector<cd> th;
+  if (!mmc::harmonic_ritz(ao.H[0], m, th)) RET(MMC_ERR_NOCONV, "harmonic Ritz eigenvalues did not converge");
+  th = mmc::leja_order(th);
+  for (auto& t : th)
+    if (!std::isfinite(t.real()) || !std::isfinite(t.imag()) || t == cd(0, 0)) RET(MMC_ERR_NAN, "bad Ritz value");
+  Poly P;
+  P.kind = 0;
+  P.theta = th;
+  P.op = op_handle;
+  ctx->polys.push_back(P);
+  *handle = int(ctx->polys.size()) - 1;
+  if (theta_out)
+    for (int i = 0; i < m; ++i) {
+      theta_out[2 * i] = th[i].real();
+      theta_out[2 * i + 1] = th[i].imag();
+    }
   return MMC_OK;
 }
 

@@ -264,6 +264,10 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
           break;
         }
         unsigned char* dst = ownb + size_t(b) * slotB;
+        if (*abort_flag) {  // a compute warp gave up: issue no further copy
+          ok = false;
+          break;
+        }
         if (copies) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           bar_expect(ofull0 + 8 * b, slotB);
@@ -280,6 +284,10 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
         const int nr = nbr_row(p, row, k);
         const bool with_links = (k & 1) != 0;
         unsigned char* dst = ringb + size_t(slot) * slotB;
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
         if (copies) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           bar_expect(full0 + 8 * slot, rowB + (with_links ? linkB : 0u));
@@ -293,11 +301,16 @@ __global__ void __launch_bounds__(max_threads<RPT>(), 1) step3_kernel(step_param
       *abort_flag = 1;
       atomicExch(p.err, 1);
     }
-    // the last copies issued into each slot land before this thread (and so the CTA) leaves
+    // the last copies issued into each slot land before this thread (and so the CTA) leaves;
+    // if one of these bounded waits gives up, a copy may still be writing into this CTA's
+    // shared memory after it exits: the flag value 2 tells the host to retire the context
     if (copies) {
+      bool drained = true;
       for (long long d = (e > ns ? e - ns : 0); d < e; ++d)
-        bar_wait(full0 + 8 * int(d % ns), uint32_t((d / ns) & 1), lim);
-      for (int d = (j > 2 ? j - 2 : 0); d < j; ++d) bar_wait(ofull0 + 8 * (d & 1), uint32_t((d >> 1) & 1), lim);
+        drained = bar_wait(full0 + 8 * int(d % ns), uint32_t((d / ns) & 1), lim) && drained;
+      for (int d = (j > 2 ? j - 2 : 0); d < j; ++d)
+        drained = bar_wait(ofull0 + 8 * (d & 1), uint32_t((d >> 1) & 1), lim) && drained;
+      if (!drained) atomicExch(p.err, 2);
     }
     return;
   }

@@ -69,6 +69,16 @@ class mmc_profile_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class mmc_profile_class(ctypes.Structure):
+    _fields_ = [("kind", _i), ("prec", _i), ("nrhs_padded", _i), ("launches", ctypes.c_longlong), ("ms", _d),
+                ("bytes", _d), ("flops", _d)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PROF_KINDS = {0: "plain", 1: "bilinear", 2: "accumulate", 3: "aux"}
+
 _SIGS = {
     "mmc_create": (_i, [ctypes.POINTER(_vp), _ip, _u64, _i]),
     "mmc_destroy": (_i, [_vp]),
@@ -107,6 +117,7 @@ _SIGS = {
     "mmc_net_train": (_i, [_vp, _i, _vp, _vp, _i, _i, _i, _d, _dp]),
     "mmc_profile": (_i, [_vp, _i]),
     "mmc_profile_read": (_i, [_vp, ctypes.POINTER(mmc_profile_stats)]),
+    "mmc_profile_classes": (_i, [_vp, _i, ctypes.POINTER(mmc_profile_class), _ip]),
     "mmc_update_gauge": (_i, [_vp, _dp]),
     "mmc_set_step_variant": (_i, [_vp, _i, _i, _i, _i]),
     "mmc_set_step_variant_class": (_i, [_vp, _i, _i, _i, _i, _i, _i, _i, _i]),
@@ -122,6 +133,7 @@ _SIGS = {
     "mmc_eig": (_i, [_i, _dp, _i, _dp, _dp]),
     "mmc_deflation_pairs": (_i, [_i, _dp, _dp, _d, _i, _ip, _ip, _ip]),
     "mmc_set_deflation_bound": (_i, [_vp, _d]),
+    "mmc_gmres_poly_deflated": (_i, [_vp, _i, _i, _dp, _ip]),
     "mmc_probe_colouring": (_i, [_ip, _i, _ip, _ip]),
     "mmc_deflation_condition": (_i, [_i, _dp, _i, _ip, _d, _ip, _ip]),
 }
@@ -539,3 +551,25 @@ def mmc_probe_colouring(dims, reach):
     n = ctypes.c_int(0)
     _check(lib.mmc_probe_colouring(d, int(reach), colour.ctypes.data_as(_ip), ctypes.byref(n)))
     return colour, n.value
+
+
+def mmc_profile_classes(ctx):
+    """Per-class step-kernel counters (list of dicts; kind named by PROF_KINDS)."""
+    n = ctypes.c_int(0)
+    _check(lib.mmc_profile_classes(ctx, 0, None, ctypes.byref(n)), ctx)
+    arr = (mmc_profile_class * max(1, n.value))()
+    _check(lib.mmc_profile_classes(ctx, n.value, arr, ctypes.byref(n)), ctx)
+    out = []
+    for i in range(n.value):
+        d = arr[i].as_dict()
+        d["kind"] = PROF_KINDS.get(d["kind"], str(d["kind"]))
+        out.append(d)
+    return out
+
+
+def mmc_gmres_poly_deflated(ctx, m, op_handle=MMC_OP_M):
+    """(handle, theta): GMRES(m) polynomial from the start vector with the deflated eigenvectors removed."""
+    theta = np.zeros(2 * int(m))
+    h = ctypes.c_int()
+    _check(lib.mmc_gmres_poly_deflated(ctx, int(m), int(op_handle), theta.ctypes.data_as(_dp), ctypes.byref(h)), ctx)
+    return h.value, theta[0::2] + 1j * theta[1::2]

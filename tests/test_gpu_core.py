@@ -187,17 +187,19 @@ def test_double_poly(mmc, lat):
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("ver,rpt,minb", [(1, 1, 1), (1, 2, 3), (2, 1, 4), (2, 1, 6), (2, 2, 3),
                                           (3, 1, 300), (3, 1, 302), (3, 2, 300),
-                                          (4, 1, 4), (4, 1, 3), (4, 1, 401)])
+                                          (4, 1, 4), (4, 1, 3), (4, 1, 401), (5, 1, 303), (5, 1, 304),
+                                          (5, 1, 306)])
 @pytest.mark.parametrize("nrhs", [5, 21])
 def test_step_kernel_variants(mmc, lat, prec, ver, rpt, minb, nrhs):
     """Every step-kernel version (generic, compile-time rhs block, rows staged by bulk
     copies with the deepest and the shallowest ring, one or two rhs per lane, the
-    persistent pipelined form with either register cap and with evict-first stores),
-    lane widths and register caps give M x, and M^+ x for the staged and persistent forms."""
+    persistent pipelined form with either register cap and with evict-first stores, the
+    form with operands staged by asynchronous copies at each pipeline depth), lane widths
+    and register caps give M x, and M^+ x for the staged and persistent forms."""
     mmc.mmc_set_step_variant(lat.ctx, prec, rpt, 100 + ver, 0)
     mmc.mmc_set_step_variant(lat.ctx, prec, 0, minb, 0)
     try:
-        if ver in (3, 4):
+        if ver in (3, 4, 5):
             rng_x = synth.random_spinor(lat.dims, 10, nrhs).transpose(6, 0, 1, 2, 3, 4, 5).reshape(nrhs, -1)
             x = mmc.new_field(lat.ctx, nrhs, prec)
             y = mmc.new_field(lat.ctx, nrhs, prec)
@@ -248,7 +250,7 @@ def test_step_variant_per_rhs_class(mmc, lat, prec):
             for j in range(nrhs):
                 want = lat.op(xin[j])
                 assert np.linalg.norm(got[j] - want) / np.linalg.norm(want) < tol
-        for bad in ({"rpt": 3}, {"version": 5}, {"ns": 7}, {"spc": 48}, {"blocked": 3}):
+        for bad in ({"rpt": 3}, {"version": 6}, {"ns": 7}, {"spc": 48}, {"blocked": 3}):
             with pytest.raises(mmc.MMCError):
                 mmc.mmc_set_step_variant_class(lat.ctx, prec, 0, dict(staged, **bad))
     finally:
@@ -257,13 +259,13 @@ def test_step_variant_per_rhs_class(mmc, lat, prec):
         mmc.mmc_set_step_variant(lat.ctx, prec, 0, 300, 0)
 
 
-@pytest.mark.parametrize("prec,ver", [(0, 1), (1, 2), (2, 2), (1, 4), (2, 4)])
+@pytest.mark.parametrize("prec,ver", [(0, 1), (1, 2), (2, 2), (1, 4), (2, 4), (1, 5), (2, 5)])
 def test_chain_graphs_replay_identical(mmc, lat, prec, ver):
     """A step chain replayed from its captured CUDA graph gives the same bits as the
     chain launched degree by degree, for p(M) X and for the level samples (whose
     partial sums the persistent form accumulates per CTA over its work items)."""
     import torch
-    mmc.mmc_set_step_variant(lat.ctx, prec, 1 if ver == 4 else 0, 100 + ver, 0)
+    mmc.mmc_set_step_variant(lat.ctx, prec, 1 if ver >= 4 else 0, 100 + ver, 0)
     theta = mmc.mmc_leja_order(1.0 + 0.7 * np.exp(2j * np.pi * (np.arange(6) + 0.5) / 6))
     h = mmc.mmc_poly_from_roots(lat.ctx, theta)
     h2 = mmc.mmc_poly_from_roots(lat.ctx, theta[:3])

@@ -39,7 +39,7 @@ THETA = np.array([1.0 + 0.8j, 1.0 - 0.8j, 0.3 + 0.0j])  # p of degree 2 (two mat
 # (version, rpt, minb, traversal, store hint) of the forms exercised: v2 lane widths, v3 thread
 # widths, v4 register caps, traversals (0 lexicographic, 1 4D blocks, 2 z-halves) and hints
 FORMS = [(2, 1, 4, 0, 0), (2, 2, 3, 0, 0), (3, 1, 1, 0, 0), (3, 2, 1, 0, 0),
-         (4, 1, 4, 0, 0), (4, 1, 3, 2, 1), (4, 1, 4, 1, 1)]
+         (4, 1, 4, 0, 0), (4, 1, 3, 2, 1), (4, 1, 4, 1, 1), (5, 1, 4, 0, 0), (5, 1, 4, 2, 0)]
 
 
 @pytest.fixture(scope="module")
@@ -138,7 +138,7 @@ def _golden():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("form", [FORMS[0], FORMS[4], FORMS[5]])
+@pytest.mark.parametrize("form", [FORMS[0], FORMS[4], FORMS[5], FORMS[7]])
 def test_benchmark_levels_full_size(mmc, big, form):
     """The level chains the benchmark runs at 24^4, in FP32 storage, against samples the
     oracle computed once (tests/golden/make_c4_levels.py): p_32 - p_8 over 512 noises,

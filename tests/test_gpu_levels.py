@@ -65,7 +65,7 @@ def _oracle_samples(L, hi, lo, theta_name, n, level, first=0):
     return np.array([o[0] for o in out]), np.array([o[1] for o in out])
 
 
-@pytest.mark.parametrize("ver,blocked", [(1, 0), (2, 0), (2, 1), (3, 0), (4, 0), (4, 1)])
+@pytest.mark.parametrize("ver,blocked", [(1, 0), (2, 0), (2, 1), (3, 0), (4, 0), (4, 1), (5, 0), (5, 1)])
 @pytest.mark.parametrize("theta_name", ["1", "g4"])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5), (2, 5e-2)])
 def test_level_poly_difference(mmc, lat, theta_name, prec, tol, ver, blocked):
