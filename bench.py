@@ -95,10 +95,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def level_plan(h):
-    """(hi, lo, deflate, n_noise, level id) of the four Monte Carlo levels."""
+def level_plan(h, top_deflated=False):
+    """(hi, lo, deflate, n_noise, level id) of the four Monte Carlo levels; the top level
+    M^-1 - p_dbl is deflated with the deflated double polynomial."""
     from paper_2402_00016_gb300 import mmc
-    return [(mmc.MMC_INV, h["dbl"], 0, 8, 1), (h["dbl"], h["p128"], 1, 32, 2),
+    return [(mmc.MMC_INV, h["dbl"], 1 if top_deflated else 0, 8, 1), (h["dbl"], h["p128"], 1, 32, 2),
             (h["p128"], h["p32"], 1, 128, 3), (h["p32"], h["p8"], 1, 512, 4)]
 
 
@@ -245,6 +246,17 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
                     help="spinor storage of the polynomial chains (BF16 rounding shifts the level samples by "
                          "several standard errors on this workload: see error_vs_fp64)")
+    ap.add_argument("--outer-m", type=int, default=8, help="outer GMRES length of the double polynomial")
+    ap.add_argument("--dbl-deflated", action="store_true",
+                    help="deflated double polynomial (outer cycle from the deflated start vector) and a deflated "
+                         "top level")
+    ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
+                    help="rounding of BF16 chain storage (stochastic keeps the BF16 levels unbiased)")
+    ap.add_argument("--learned", action="store_true",
+                    help="the learned form: a BF16 network trained on 16^4 solve pairs as the M^-1 level's "
+                         "preconditioner and as an extra level p_8 - N with Tr(N) exact")
+    ap.add_argument("--learned-pairs", type=int, default=4096)
+    ap.add_argument("--learned-iters", type=int, default=1500)
     ap.add_argument("--cpu-reps", type=int, default=4, help="degree-2 oracle samples of the one-core leg")
     ap.add_argument("--plain-samples", type=int, default=4,
                     help="FP64 single-vector samples per level for the plain form")
@@ -278,8 +290,9 @@ def main():
     mmc.mmc_load_gauge(ctx, U, W.kappa, W.t_antiperiodic)
     h = {}
     h["in"], _ = mmc.mmc_gmres_poly(ctx, 40)
-    h["out"], _ = mmc.mmc_gmres_poly(ctx, 8, h["in"])
-    h["dbl"] = mmc.mmc_poly_double(ctx, h["in"], h["out"])
+    if not args.dbl_deflated:
+        h["out"], _ = mmc.mmc_gmres_poly(ctx, args.outer_m, h["in"])
+        h["dbl"] = mmc.mmc_poly_double(ctx, h["in"], h["out"])
     h["p128"], _ = mmc.mmc_gmres_poly(ctx, 129)
     h["p32"], _ = mmc.mmc_gmres_poly(ctx, 33)
     h["p8"], _ = mmc.mmc_gmres_poly(ctx, 9)
@@ -302,16 +315,57 @@ def main():
         if args.tune_file:
             with open(args.tune_file, "w") as f:
                 json.dump(tune, f)
+    mmc.mmc_set_rounding(ctx, mmc.MMC_ROUND_STOCHASTIC if args.rounding == "stochastic" else mmc.MMC_ROUND_NEAREST,
+                         seed=W.noise_seed)
     mmc.mmc_set_solve_params(ctx, args.solve_m, 400)
     mmc.mmc_set_solve_storage(ctx, mmc.PREC[args.solve_storage])
     t_poly = time.time() - t_setup
     lam = mmc.mmc_deflate(ctx, args.deflate_k, h["in"], args.arnoldi, 1e-3) if args.deflate_k > 0 else []
+    if args.dbl_deflated:
+        # the deflated double polynomial: p_out from the start vector without the deflated
+        # eigenvector components; the top level is then deflated too
+        h["out"], _ = mmc.mmc_gmres_poly_deflated(ctx, args.outer_m, h["in"])
+        h["dbl"] = mmc.mmc_poly_double(ctx, h["in"], h["out"])
     pre = h[args.precond]
+    pre_plain = pre  # the plain FP64 form keeps the polynomial preconditioner
     t_defl = time.time() - t_setup - t_poly
-    exact = mmc.mmc_trace_exact(ctx, h["p8"], mmc.MMC_THETA_ONE, mmc.MMC_EXACT_PROBE, mmc.MMC_F64)
-    ncol = mmc.mmc_probe_colours(ctx, 8)
+    learned_info = None
+    if args.learned:
+        # the learned form: a network trained on (eta, M^-1 eta) pairs from 16^4 solves of
+        # fields drawn with this workload's eps and kappa (BF16 weights and activations),
+        # as the right preconditioner of the M^-1 level's solves and as the operand of an
+        # extra Monte Carlo level p_8 - N whose exact last level Tr(N) replaces Tr(p_8)
+        from paper_2402_00016_gb300 import learned_train
+        t0 = time.time()
+        dims16 = (16, 16, 16, 16)
+        c16 = mmc.mmc_create(dims16, seed=W.noise_seed + 100, device=local)
+        try:
+            mmc.mmc_load_gauge(c16, synth.random_gauge(dims16, W.eps, W.gauge_seed + 1), W.kappa, 1)
+            hp16, _ = mmc.mmc_gmres_poly(c16, 40)
+            lam16 = mmc.mmc_deflate(c16, 40, hp16, 200, 1e-3)
+            eta16, xs16, solves = learned_train.make_pairs(mmc, c16, args.learned_pairs, precond=hp16)
+            hn16, hist = learned_train.train(mmc, c16, eta16, xs16, args.learned_pairs, iters=args.learned_iters)
+            weights = mmc.mmc_net_get_weights(c16, hn16)
+            del eta16, xs16
+        finally:
+            mmc.mmc_destroy(c16)
+        h["net"] = mmc.mmc_net_create(ctx, weights)
+        mmc.mmc_net_set_precision(ctx, h["net"], mmc.MMC_BF16)
+        pre = h["net"]
+        learned_info = {"train_pairs": args.learned_pairs, "train_lattice": "16^4", "deflated_16": len(lam16),
+                        "pair_solves": solves, "iters": args.learned_iters, "loss_first": float(np.mean(hist[:10])),
+                        "loss_last": float(np.mean(hist[-10:])), "seconds": time.time() - t0,
+                        "storage": "bf16 weights and activations, fp32 accumulation"}
+        exact = mmc.mmc_trace_exact(ctx, h["net"], mmc.MMC_THETA_ONE, mmc.MMC_EXACT_PROBE, mmc.MMC_F32)
+        ncol = mmc.mmc_probe_colours(ctx, 3)
+    else:
+        exact = mmc.mmc_trace_exact(ctx, h["p8"], mmc.MMC_THETA_ONE, mmc.MMC_EXACT_PROBE, mmc.MMC_F64)
+        ncol = mmc.mmc_probe_colours(ctx, 8)
     t_setup = time.time() - t_setup
-    plan = level_plan(h)
+    plan = level_plan(h, args.dbl_deflated)
+    if args.learned:
+        plan.append((h["p8"], h["net"], 0, 512, 5))
+    samples_per_step = sum(n for (_, _, _, n, _) in plan)
 
     def step(it):
         out = []
@@ -346,7 +400,7 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
-    samples = SAMPLES * args.steps * world
+    samples = samples_per_step * args.steps * world
     value = samples / (ms_max / 1e3)
 
     # end to end: gauge configuration from pinned host memory every step, samples read back
@@ -360,7 +414,7 @@ def main():
         _ = [r["samples"].copy() for r in res]
     barrier()
     e2e_s = time.time() - t0
-    e2e_val = samples / e2e_s if world == 1 else SAMPLES * args.steps / e2e_s * world
+    e2e_val = samples / e2e_s if world == 1 else samples_per_step * args.steps / e2e_s * world
 
     # statistics of the last timed step (trace error of the estimator), merged over replicas
     last = results[-1]
@@ -380,18 +434,18 @@ def main():
             for q in range(args.plain_samples):
                 torch.cuda.synchronize()
                 t0 = time.time()
-                mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, 1, 900_000 + q, lvl, mmc.MMC_F64, pre,
-                                    want_samples=False)
+                mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, 1, 900_000 + q, lvl, mmc.MMC_F64,
+                                    pre_plain, want_samples=False)
                 torch.cuda.synchronize()
                 ts.append(time.time() - t0)
             per_sample.append(float(np.mean(ts)))
             spread.append([float(np.min(ts)), float(np.max(ts))])
         t_step = sum(n * t for (_, _, _, n, _), t in zip(plan, per_sample))
-        plain = {"value": SAMPLES / t_step, "unit": "samples/s", "seconds_per_sample_by_level": per_sample,
+        plain = {"value": samples_per_step / t_step, "unit": "samples/s", "seconds_per_sample_by_level": per_sample,
                  "min_max_seconds_by_level": spread,
                  "sample": "%d FP64 single-vector samples per level (host wall time each), their mean "
                            "extrapolated to the 8/32/128/512 mix" % args.plain_samples,
-                 "speedup_of_value": value / (SAMPLES / t_step)}
+                 "speedup_of_value": value / (samples_per_step / t_step)}
 
     # Error of the reduced-precision form against the FP64 form (which the parity tests pin
     # to the oracle): the same noises through both, per level; bias in units of the level's
@@ -402,7 +456,7 @@ def main():
         for (hi, lo, defl, n, lvl), r in zip(plan, last):
             q = 1 if hi == mmc.MMC_INV else min(n, 4)  # the FP64 solves are the costly part
             a = mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, q, 800_000, lvl, storage, pre)
-            b = mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, q, 800_000, lvl, mmc.MMC_F64, pre)
+            b = mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, q, 800_000, lvl, mmc.MMC_F64, pre_plain)
             d = a["samples"] - b["samples"]
             se = float(np.sqrt(r["var_re"] / n)) if r["var_re"] > 0 else float("nan")
             err_vs_fp64.append({"noises": q, "max_abs_sample_diff": float(np.abs(d).max()),
@@ -442,8 +496,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": "24^4", "eps": W.eps, "kappa": W.kappa,
-                   "levels": LEVELS,
-                   "noises": [8, 32, 128, 512], "storage": args.storage, "arithmetic": "fp32, fp64 bilinears",
+                   "levels": LEVELS + (["p_8 - N (learned)"] if args.learned else []), "double": {"m_in": 40, "m_out": args.outer_m, "deflated": args.dbl_deflated},
+                   "noises": [n for (_, _, _, n, _) in plan], "storage": args.storage, "rounding": args.rounding, "arithmetic": "fp32, fp64 bilinears",
                    "deflated": len(lam), "probe_colours": ncol,
                    "solves": {"fgmres_m": args.solve_m, "precond": "p_in (degree 39)" if args.precond == "in"
                               else "p_dbl (degree 319)", "tol": 1e-10, "inner_storage": args.solve_storage}, "l2": "inputs larger than L2 (GB-sized fields)",
@@ -475,9 +529,10 @@ def main():
         "launch_index_timed_start": launches_before,
         "e2e": {"value": e2e_val, "unit": "samples/s",
                 "h2d_bytes_per_step": int(U.nbytes),
-                "d2h_bytes_per_step": int(SAMPLES * 16)},
+                "d2h_bytes_per_step": int(samples_per_step * 16)},
         "clocks": clk.summary(),
         "setup_s": {"total": t_setup, "polynomials_and_tuning": t_poly, "deflation": t_defl},
+        "learned": learned_info,
         "autotune": tune,
         "estimate": {"trace_re": est, "stderr": stderr, "exact_last_level": exact.real,
                      "per_level_var": [r["var_re"] for r in last],

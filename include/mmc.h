@@ -126,6 +126,11 @@ int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiod
 int mmc_pack(mmc_ctx* ctx, const double* host, int nrhs, int prec, void* field);
 int mmc_unpack(mmc_ctx* ctx, const void* field, int nrhs, int prec, double* host);
 
+/* dst = src element by element between storage precisions (rounding to nearest),
+ * nrhs vectors in the blocked layout of both (not part of the paper: data
+ * movement, e.g. FP64 solutions into an FP32 training set).  src != dst. */
+int mmc_convert(mmc_ctx* ctx, const void* src, int src_prec, void* dst, int dst_prec, int nrhs, void* stream);
+
 /* y = M x (dagger = 0) or y = M^+ x (dagger = 1) for nrhs vectors of precision
  * prec (Sec. 1, Eq. 1's Wilson-Dirac matrix).  x and y must not overlap. */
 int mmc_apply_M(mmc_ctx* ctx, const void* x, void* y, int nrhs, int prec, int dagger,
@@ -327,6 +332,13 @@ int mmc_probe_colouring(const int dims[4], int reach, int* colour, int* n_colour
 int mmc_net_create(mmc_ctx* ctx, const double* weights, uint64_t seed, int* handle);
 int mmc_net_set_weights(mmc_ctx* ctx, int handle, const double* weights);
 int mmc_net_get_weights(mmc_ctx* ctx, int handle, double* weights);
+/* Storage of the network's weights and hidden activations (spec precision
+ * form): MMC_F32 (default) or MMC_BF16 (weights rounded to BF16 from the FP64
+ * master copy, the 24-component hidden activations stored in BF16; FP32
+ * arithmetic and accumulation; the input and output fields stay MMC_F32).  Both
+ * inference and training use it; training keeps FP64 master weights (Adam on the
+ * host) and FP32 gradients of the BF16 forward pass. */
+int mmc_net_set_precision(mmc_ctx* ctx, int handle, int prec);
 /* y = N x for nrhs MMC_F32 vectors (inference kernels, FP32 arithmetic). */
 int mmc_net_apply(mmc_ctx* ctx, int handle, const void* x, void* y, int nrhs, void* stream);
 /* Loss L = (1/B) sum_b ||N eta_b - x_b||^2 / ||x_b||^2 on one batch of B = nrhs
@@ -395,6 +407,19 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
  * iteration tolerates the less accurate preconditioner at the cost of more
  * iterations.  MMC_ERR_ARG for any other value. */
 int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner);
+/* Rounding of BF16 chain storage (spec precision form; not in the paper):
+ * mode 0 rounds every stored element to nearest (default); mode 1 rounds it up or
+ * down with probability given by its discarded bits, with random bits from a
+ * counter-based hash of (element, step, a per-chain salt held in device memory and
+ * advanced by each chain's first launch, so graph replays get fresh bits too),
+ * which makes every stored iterate an unbiased estimate of the exact one and, the
+ * chains and bilinears being linear, keeps each BF16 level unbiased.  seed sets the
+ * salt sequence (results are reproducible for the same seed and call sequence).
+ * The staged kernel form (version 3) is replaced by version 2 in mode 1.
+ * MMC_ERR_ARG for other modes. */
+enum { MMC_ROUND_NEAREST = 0, MMC_ROUND_STOCHASTIC = 1 };
+int mmc_set_rounding(mmc_ctx* ctx, int mode, uint64_t seed);
+
 /* Not part of the paper (data layout): largest right-hand-side block R of the
  * blocked field layout [rb][site][c][R] (8 or 16, default 16).  A batch of N vectors uses R = min(rmax, next power of
  * two >= N).  It changes the layout of every field sized or interpreted after

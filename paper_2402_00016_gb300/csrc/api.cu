@@ -69,6 +69,11 @@ int mmc_destroy(mmc_ctx* ctx) {
   if (ctx->nbr) cudaFree(ctx->nbr);
   if (ctx->order) cudaFree(ctx->order);
   if (ctx->order_zh) cudaFree(ctx->order_zh);
+  if (ctx->salt) cudaFree(ctx->salt);
+  for (auto& n : ctx->nets) {
+    if (n.dw) cudaFree(n.dw);
+    if (n.dwb) cudaFree(n.dwb);
+  }
   if (ctx->step_err) cudaFree(ctx->step_err);
   if (ctx->Z) cudaFree(ctx->Z);
   if (ctx->U) cudaFree(ctx->U);
@@ -228,6 +233,19 @@ int mmc_profile_read(mmc_ctx* ctx, mmc_profile_stats* out) {
   out->all_launches = mmc::launch_count() - ctx->launches0;
   out->graph_launches = ctx->graph_launches - ctx->graph_launches0;
   out->graph_captures = ctx->graph_captures - ctx->graph_captures0;
+  return MMC_OK;
+}
+
+int mmc_set_rounding(mmc_ctx* ctx, int mode, uint64_t seed) {
+  if (!ctx || mode < 0 || mode > 1) return MMC_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  if (mode == 1) {
+    if (!ctx->salt) CK(cudaMalloc(&ctx->salt, sizeof(uint32_t)));
+    const uint32_t v = uint32_t(seed ^ (seed >> 32)) ^ 0x2545F491u;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->salt, &v, sizeof(v), cudaMemcpyHostToDevice));
+  }
+  ctx->rounding = mode;
   return MMC_OK;
 }
 
@@ -531,6 +549,15 @@ int mmc_unpack(mmc_ctx* ctx, const void* field, int nrhs, int prec, double* host
   CK(mmc::launch_unpack(prec, g, nrhs, field, (double2*)canon, ctx->stream));
   CK(cudaMemcpyAsync(host, canon, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return MMC_OK;
+}
+
+int mmc_convert(mmc_ctx* ctx, const void* src, int src_prec, void* dst, int dst_prec, int nrhs, void* stream) {
+  if (!ctx || !src || !dst || nrhs < 1 || src_prec < 0 || src_prec > 2 || dst_prec < 0 || dst_prec > 2)
+    return MMC_ERR_ARG;
+  if (src == dst) RET(MMC_ERR_ARG, "mmc_convert: src and dst must differ");
+  CK(cudaSetDevice(ctx->device));
+  CK(mmc::launch_convert(dst_prec, dst, src_prec, src, make_geom(ctx, nrhs), static_cast<cudaStream_t>(stream)));
   return MMC_OK;
 }
 

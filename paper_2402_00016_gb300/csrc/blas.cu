@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "stencil_ops.cuh"
 
 namespace mmc {
 namespace {
@@ -673,6 +674,38 @@ static void convert_from(int ps, size_t n, D* dst, const void* src, cudaStream_t
     convert_kernel<D, float2><<<blocks, 256, 0, s>>>(n, dst, (const float2*)src);
   else
     convert_kernel<D, __nv_bfloat162><<<blocks, 256, 0, s>>>(n, dst, (const __nv_bfloat162*)src);
+}
+
+// FP32 -> BF16 with stochastic rounding, stream key from *salt (a different stream
+// from the step kernels' keys of the same salt)
+__global__ void convert_sr_kernel(size_t n, __nv_bfloat162* dst, const float2* src, const uint32_t* salt) {
+  const uint32_t key = __ldg(salt) ^ 0x5bd1e995u;
+  size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  for (; i < n; i += stride) {
+    const float2 v = src[i];
+    const uint32_t r = sten::sr_bits(uint32_t(i), key);
+    reinterpret_cast<uint32_t*>(dst)[i] = sten::bf16_bits_sr(v.x, r) | (sten::bf16_bits_sr(v.y, r >> 16) << 16);
+  }
+}
+
+__global__ void salt_advance_kernel(uint32_t* salt) {
+  // one step of a 32-bit linear congruential sequence (Numerical Recipes constants)
+  *salt = *salt * 1664525u + 1013904223u;
+}
+
+cudaError_t launch_convert_sr(void* dst, const void* src, geom g, const uint32_t* salt, cudaStream_t s) {
+  const size_t n = size_t(g.nrb) * g.V * 12 * g.R;
+  const unsigned blocks = unsigned(std::min<size_t>((n + 255) / 256, 152 * 64));
+  convert_sr_kernel<<<blocks, 256, 0, s>>>(n, (__nv_bfloat162*)dst, (const float2*)src, salt);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_salt_advance(uint32_t* salt, cudaStream_t s) {
+  salt_advance_kernel<<<1, 1, 0, s>>>(salt);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_convert(int pd, void* dst, int ps, const void* src, geom g, cudaStream_t s) {

@@ -42,6 +42,7 @@ struct step_params {
   long long wait_iters;    // bound of each mbarrier wait of the staged form (0: the default)
   int stall_test;          // fault injection: the staged form's producer issues no copies
   int hint;                // bit 0: store the result with an L2 evict-first policy (fourth form)
+  const uint32_t* salt;    // non-null: BF16 results stochastically rounded, stream key from *salt and step
 };
 
 template <typename T>

@@ -36,6 +36,8 @@ struct DevBuf {
 struct Net {
   std::vector<std::complex<double>> w;  // 1152 complex
   float2* dw = nullptr;                 // device copy, same order
+  __nv_bfloat162* dwb = nullptr;        // BF16 device copy (BF16 network)
+  bool bf16 = false;                    // BF16 weights and hidden activations, FP32 accumulation
 };
 constexpr int kNetCh[4] = {4, 8, 8, 4};
 constexpr int kNetWeights = 9 * (8 * 4 + 8 * 8 + 4 * 8);
@@ -89,6 +91,8 @@ struct mmc_ctx {
   long long graph_captures = 0, graph_captures0 = 0;
   std::string graph_note;             // why graphs were switched off, if they were
   bool failed = false;         // set when a kernel may have left work in flight: every later call refuses
+  int rounding = 0;            // BF16 chain storage: 0 round to nearest, 1 stochastic (mmc_set_rounding)
+  uint32_t* salt = nullptr;    // device word: stochastic-rounding salt, advanced once per BF16 chain
   double defl_max_u = 100.0;  // mmc_deflate: bound on the norm of a left vector u_i (a column of (W^H Z)^{-H})
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
@@ -339,8 +343,14 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       cls = int(ctx->prof_classes.size()) - 1;
     }
   }
+  // stochastic rounding of BF16 chains: a fresh salt per chain application, advanced on
+  // the device by the chain's first launch (so a replayed graph advances it too)
+  const bool sr = ctx->rounding == 1 && run.prec == MMC_BF16 && ctx->salt;
+  // the staged form (3) rounds to nearest only: stochastic rounding runs the second form
+  const int ver_run = (sr && ctx->var_ver[run.prec][rc] == 3) ? 2 : ctx->var_ver[run.prec][rc];
   // one launch per step; with per-launch profiling events unless the chain is captured
   auto launch_steps = [&](bool events, cudaStream_t s) -> int {
+    if (sr) CK(mmc::launch_salt_advance(ctx->salt, s));
     for (size_t k = 0; k < run.steps.size(); ++k) {
       const Step& st = run.steps[k];
       mmc::step_params p;
@@ -358,6 +368,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       p.nbr = ctx->nbr;
       p.order = ctx->order_v[run.prec][rc] == 1 ? ctx->order : ctx->order_v[run.prec][rc] == 2 ? ctx->order_zh : nullptr;
       p.hint = ctx->var_hint[run.prec][rc];
+      p.salt = sr ? ctx->salt : nullptr;
       p.step = int(k);
       p.V = ctx->V;
       p.R = g.R;
@@ -381,7 +392,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
         CK(cudaEventRecord(e0, s));
       }
       bool done = false;
-      if (ctx->var_ver[run.prec][rc] == 5 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      if (ver_run == 5 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e5 = cudaSuccess;
         const int ns = ctx->var_ns[run.prec][rc];
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
@@ -389,7 +400,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
                                    : mmc::launch_step5_bf16(g.R, ns == 6 ? 6 : 4, p, g.nrb, nbx, s, &e5);
         CK(e5);
       }
-      if (!done && ctx->var_ver[run.prec][rc] == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      if (!done && ver_run == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e4 = cudaSuccess;
         const int mb = ctx->var_minb[run.prec][rc] == 3 ? 3 : 4;
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
@@ -397,12 +408,12 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
                                    : mmc::launch_step4_bf16(g.R, mb, p, g.nrb, nbx, s, &e4);
         CK(e4);
       }
-      if (!done && ctx->var_ver[run.prec][rc] == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      if (!done && ver_run == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e3 = cudaSuccess;
         done = mmc::launch_step3(run.prec, g.R, rpt, run.nbx, ctx->var_ns[run.prec][rc], p, g.nrb, s, &e3);
         CK(e3);
       }
-      if (!done && ctx->var_ver[run.prec][rc] >= 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      if (!done && ver_run >= 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e2 = cudaSuccess;
         const int mb = ctx->var_minb[run.prec][rc];
         done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, mb, p, g.nrb, s, &e2)
@@ -438,7 +449,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     mix(reinterpret_cast<uintptr_t>(run.prec == MMC_F64 ? ctx->links64 : ctx->links32));
     mix(uint64_t(run.theta) | (uint64_t(run.nbx) << 8) | (uint64_t(run.dagger) << 40) | (uint64_t(run.prec) << 48));
     mix(uint64_t(g.npad) | (uint64_t(g.R) << 32) | (uint64_t(ctx->stall_test) << 63));
-    mix(uint64_t(ctx->wait_iters));
+    mix(uint64_t(ctx->wait_iters) ^ (uint64_t(sr) << 62));
     mix(uint64_t(ctx->var_ver[run.prec][rc]) | (uint64_t(rpt) << 8) | (uint64_t(ctx->var_minb[run.prec][rc]) << 16) |
         (uint64_t(ctx->spc_v[run.prec][rc]) << 24) | (uint64_t(ctx->order_v[run.prec][rc]) << 40) |
         (uint64_t(ctx->var_ns[run.prec][rc]) << 48) | (uint64_t(ctx->var_hint[run.prec][rc]) << 56));
@@ -751,7 +762,10 @@ inline int apply_poly_impl(mmc_ctx* ctx, int h, const void* x, int nrhs, int pre
     build_single(ctx, run, tin, x, P0, P1, ACC_Y, 1.0, nrhs);
     TRY(exec_run(ctx, run, s));
   }
-  CK(mmc::launch_convert(prec, A0, prec == MMC_F64 ? MMC_F64 : MMC_F32, W, g, s));
+  if (prec == MMC_BF16 && ctx->rounding == 1 && ctx->salt)
+    CK(mmc::launch_convert_sr(A0, W, g, ctx->salt, s));
+  else
+    CK(mmc::launch_convert(prec, A0, prec == MMC_F64 ? MMC_F64 : MMC_F32, W, g, s));
   Run run = base;
   run.y = y;
   build_double_outer(ctx, run, tin, tout, P0, P1, A0, A1, mode, nrhs);
@@ -852,7 +866,7 @@ inline int apply_op_f64(mmc_ctx* ctx, int op_handle, const void* in, void* out, 
 
 // learned network (learned.cu)
 bool is_net(const mmc_ctx* ctx, int h);
-int net_apply(mmc_ctx* ctx, int h, const void* x, void* y, int nrhs, cudaStream_t s, float2** acts);
+int net_apply(mmc_ctx* ctx, int h, const void* x, void* y, int nrhs, cudaStream_t s, void** acts);
 
 inline int check_ctx(mmc_ctx* ctx) {
   if (!ctx) return MMC_ERR_ARG;

@@ -59,6 +59,11 @@ cudaError_t launch_probe(int prec, geom g, const int* site_colour, const int2* p
 cudaError_t launch_pack(int prec, geom g, int nrhs, const double2* canon, void* field, cudaStream_t s);
 cudaError_t launch_unpack(int prec, geom g, int nrhs, const void* field, double2* canon, cudaStream_t s);
 
+// BF16 dst = FP32 src rounded stochastically (stream key from *salt, device memory).
+cudaError_t launch_convert_sr(void* dst, const void* src, geom g, const uint32_t* salt, cudaStream_t s);
+// *salt advances one step of its sequence (a fresh stochastic-rounding stream per chain).
+cudaError_t launch_salt_advance(uint32_t* salt, cudaStream_t s);
+
 // dst (precision pd) = src (precision ps), same geometry.
 cudaError_t launch_convert(int pd, void* dst, int ps, const void* src, geom g, cudaStream_t s);
 
@@ -111,12 +116,15 @@ struct net_geom {
   int L[4];
   const void* links;
 };
-// out = layer(in) for (ci, co) in {(4,8), (8,8), (8,4), (4,4)}; W: 9 x co x ci complex FP32.
-cudaError_t launch_net_layer(const net_geom& g, int ci, int co, const float2* in, const float2* W, float2* out,
-                             cudaStream_t s);
-// partial[b][9][co][ci] over b = rb * nbx + bx: sum delta conj(feature) (weight gradients).
-cudaError_t launch_net_wgrad(const net_geom& g, int ci, int co, const float2* in, const float2* delta, int spc,
-                             double2* partial, cudaStream_t s);
+// out = layer(in) for (ci, co) in {(4,8), (8,8), (8,4), (4,4)}; W: 9 x co x ci complex, FP32
+// (float2) or BF16 (two bfloat16); in and out FP32 or BF16 activations (FP32 weights only
+// with FP32 activations); FP32 arithmetic.
+cudaError_t launch_net_layer(const net_geom& g, int ci, int co, const void* in, bool in_bf16, const void* W,
+                             bool w_bf16, void* out, bool out_bf16, cudaStream_t s);
+// partial[b][9][co][ci] over b = rb * nbx + bx: sum delta conj(feature) (weight gradients);
+// the layer input FP32 or BF16, delta FP32.
+cudaError_t launch_net_wgrad(const net_geom& g, int ci, int co, const void* in, bool in_bf16, const float2* delta,
+                             int spc, double2* partial, cudaStream_t s);
 
 // Tensor-core deflation projections (tc_proj.cu): BF16 copy of [Theta z; u] (256 x Kp),
 // the correction dots from that copy, and the projections P (FP64, rows 2 npad padded

@@ -39,15 +39,28 @@ net_geom ngeom(const mmc_ctx* ctx, const geom& g) {
   return n;
 }
 
+// BF16 rounding of a weight (round to nearest even on the float value), on the host
+float bf16_round(double v) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(float(v));
+  return __bfloat162float(b);
+}
+
 int upload_net(mmc_ctx* ctx, Net& N) {
   std::vector<float2> h(kNetWeights);
-  for (int i = 0; i < kNetWeights; ++i) h[i] = make_float2(float(N.w[i].real()), float(N.w[i].imag()));
+  std::vector<__nv_bfloat162> hb(kNetWeights);
+  for (int i = 0; i < kNetWeights; ++i) {
+    h[i] = make_float2(float(N.w[i].real()), float(N.w[i].imag()));
+    hb[i] = __floats2bfloat162_rn(float(N.w[i].real()), float(N.w[i].imag()));
+  }
   if (!N.dw) CK(cudaMalloc(&N.dw, sizeof(float2) * kNetWeights));
+  if (!N.dwb) CK(cudaMalloc(&N.dwb, sizeof(__nv_bfloat162) * kNetWeights));
   CK(cudaMemcpy(N.dw, h.data(), sizeof(float2) * kNetWeights, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(N.dwb, hb.data(), sizeof(__nv_bfloat162) * kNetWeights, cudaMemcpyHostToDevice));
   return MMC_OK;
 }
 
-// Adjoint weights of layer l (C_in x C_out blocks): W0^H, Wf[mu] <- Wb[mu]^H, Wb[mu] <- Wf[mu]^H.
+// Adjoint weights of layer l (C_in x C_out blocks): W0^H, Wf[mu] <- Wb[mu]^H, Wb[mu] <- Wf[mu]^H
+// (of the BF16-rounded weights for a BF16 network, the ones its forward pass uses).
 std::vector<float2> adjoint_weights(const Net& N, int l) {
   const int ci = kNetCh[l], co = kNetCh[l + 1];
   const int off = layer_offset(l);
@@ -57,6 +70,7 @@ std::vector<float2> adjoint_weights(const Net& N, int l) {
     for (int i = 0; i < ci; ++i)
       for (int o = 0; o < co; ++o) {
         cd v = std::conj(N.w[off + (size_t(src) * co + o) * ci + i]);
+        if (N.bf16) v = cd(bf16_round(v.real()), bf16_round(v.imag()));
         a[(size_t(w) * ci + i) * co + o] = make_float2(float(v.real()), float(v.imag()));
       }
   }
@@ -67,20 +81,24 @@ std::vector<float2> adjoint_weights(const Net& N, int l) {
 
 // y = N x on FP32 fields (12 components per site) of nrhs vectors.  Activations
 // a1, a2 (24 components) are context scratch; returned through *acts if given.
-int net_apply(mmc_ctx* ctx, int h, const void* x, void* y, int nrhs, cudaStream_t s, float2** acts) {
+int net_apply(mmc_ctx* ctx, int h, const void* x, void* y, int nrhs, cudaStream_t s, void** acts) {
   Net& N = ctx->nets[h - kNetBase];
   const geom g = make_geom(ctx, nrhs);
   const net_geom ng = ngeom(ctx, g);
-  const size_t hid = size_t(g.npad) * g.V * 24 * sizeof(float2);
+  const bool b = N.bf16;
+  const size_t hid = size_t(g.npad) * g.V * 24 * (b ? sizeof(__nv_bfloat162) : sizeof(float2));
   void *a1, *a2;
-  TRY(scratch(ctx, "net_a1", hid, &a1));
-  TRY(scratch(ctx, "net_a2", hid, &a2));
-  CK(mmc::launch_net_layer(ng, 4, 8, (const float2*)x, N.dw + layer_offset(0), (float2*)a1, s));
-  CK(mmc::launch_net_layer(ng, 8, 8, (const float2*)a1, N.dw + layer_offset(1), (float2*)a2, s));
-  CK(mmc::launch_net_layer(ng, 8, 4, (const float2*)a2, N.dw + layer_offset(2), (float2*)y, s));
+  TRY(scratch(ctx, b ? "net_a1b" : "net_a1", hid, &a1));
+  TRY(scratch(ctx, b ? "net_a2b" : "net_a2", hid, &a2));
+  const void* W0 = b ? (const void*)(N.dwb + layer_offset(0)) : (const void*)(N.dw + layer_offset(0));
+  const void* W1 = b ? (const void*)(N.dwb + layer_offset(1)) : (const void*)(N.dw + layer_offset(1));
+  const void* W2 = b ? (const void*)(N.dwb + layer_offset(2)) : (const void*)(N.dw + layer_offset(2));
+  CK(mmc::launch_net_layer(ng, 4, 8, x, false, W0, b, a1, b, s));
+  CK(mmc::launch_net_layer(ng, 8, 8, a1, b, W1, b, a2, b, s));
+  CK(mmc::launch_net_layer(ng, 8, 4, a2, b, W2, b, y, false, s));
   if (acts) {
-    acts[0] = (float2*)a1;
-    acts[1] = (float2*)a2;
+    acts[0] = a1;
+    acts[1] = a2;
   }
   return MMC_OK;
 }
@@ -99,7 +117,7 @@ int net_loss_grad(mmc_ctx* ctx, int h, const void* eta, const void* xs, int nrhs
   TRY(scratch(ctx, "net_d2", hid, &d2));
   TRY(scratch(ctx, "net_d1", hid, &d1));
   TRY(scratch(ctx, "net_aw", sizeof(float2) * 9 * 64, &aw));
-  float2* acts[2];
+  void* acts[2];
   TRY(net_apply(ctx, h, eta, out, nrhs, s, acts));
   // r = out - x ; norms
   std::vector<cd> one(g.npad, cd(1, 0)), mone(g.npad, cd(-1, 0));
@@ -141,12 +159,13 @@ int net_loss_grad(mmc_ctx* ctx, int h, const void* eta, const void* xs, int nrhs
   const int wspc = 256, wnbx = (g.V + wspc - 1) / wspc;
   const int nb_all = wnbx * g.nrb;
   TRY(scratch(ctx, "net_wpart", size_t(nb_all) * 9 * 64 * sizeof(double2), &part));
-  const float2* layer_in[3] = {(const float2*)eta, acts[0], acts[1]};
+  const void* layer_in[3] = {eta, acts[0], acts[1]};
+  const bool in_b[3] = {false, N.bf16, N.bf16};
   float2* deltas[3] = {(float2*)d1, (float2*)d2, (float2*)d3};
   for (int l = 2; l >= 0; --l) {
     const int ci = kNetCh[l], co = kNetCh[l + 1];
     const int nw = 9 * ci * co;
-    CK(mmc::launch_net_wgrad(ng, ci, co, layer_in[l], deltas[l], wspc, (double2*)part, s));
+    CK(mmc::launch_net_wgrad(ng, ci, co, layer_in[l], in_b[l], deltas[l], wspc, (double2*)part, s));
     void* wred;
     TRY(scratch(ctx, "net_wred", size_t(nw) * sizeof(double2), &wred));
     // partials were written with stride 9*co*ci per block
@@ -156,7 +175,7 @@ int net_loss_grad(mmc_ctx* ctx, int h, const void* eta, const void* xs, int nrhs
     if (l > 0) {
       std::vector<float2> aw_h = adjoint_weights(N, l);
       CK(cudaMemcpyAsync(aw, aw_h.data(), aw_h.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
-      CK(mmc::launch_net_layer(ng, co, ci, deltas[l], (const float2*)aw, deltas[l - 1], s));
+      CK(mmc::launch_net_layer(ng, co, ci, deltas[l], false, aw, false, deltas[l - 1], false, s));
     }
     CK(cudaStreamSynchronize(s));
     const int off = layer_offset(l);
@@ -212,6 +231,12 @@ int mmc_net_get_weights(mmc_ctx* ctx, int handle, double* weights) {
     weights[2 * i] = N.w[i].real();
     weights[2 * i + 1] = N.w[i].imag();
   }
+  return MMC_OK;
+}
+
+int mmc_net_set_precision(mmc_ctx* ctx, int handle, int prec) {
+  if (!ctx || !is_net(ctx, handle) || (prec != MMC_F32 && prec != MMC_BF16)) return MMC_ERR_ARG;
+  ctx->nets[handle - kNetBase].bf16 = prec == MMC_BF16;
   return MMC_OK;
 }
 

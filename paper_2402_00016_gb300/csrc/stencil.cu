@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(128, MINB) step_kernel(step_params p) {
   const int rglob = rb * p.R + r0;
   const S* in = reinterpret_cast<const S*>(p.in) + size_t(rb) * p.V * 12 * p.R;
   const int flags = p.flags;
+  const uint32_t srkey = sr_key(p);
 
   cx<T> ca[RPT], cb[RPT], cg[RPT], cwi[RPT], cwo[RPT];
 #pragma unroll
@@ -104,7 +105,13 @@ __global__ void __launch_bounds__(128, MINB) step_kernel(step_params p) {
 #pragma unroll
         for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], ax[j], vout[j]);
       }
-      if (flags & SF_WRITE) store_rpt<S, RPT>(reinterpret_cast<S*>(p.out) + boff + size_t(c) * p.R, vout);
+      if (flags & SF_WRITE) {
+        if (std::is_same<S, __nv_bfloat162>::value && p.salt)
+          store_rpt_sr<S, RPT>(reinterpret_cast<S*>(p.out) + boff + size_t(c) * p.R, vout, srkey,
+                               uint32_t(boff + size_t(c) * p.R));
+        else
+          store_rpt<S, RPT>(reinterpret_cast<S*>(p.out) + boff + size_t(c) * p.R, vout);
+      }
       if (flags & SF_YACC) {
         Y* yp = reinterpret_cast<Y*>(p.y) + boff + size_t(c) * p.R;
 #pragma unroll

@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
   const size_t rb_off = size_t(rb) * p.V * 12 * R;
   const S* in = reinterpret_cast<const S*>(p.in) + rb_off + r0;
   const bool bil_out = (p.flags & SF_BIL_OUT) != 0;
+  const uint32_t srkey = sr_key(p);
 
   cx<T> ca[RPT], cb[RPT], cg[RPT], cwi[RPT], cwo[RPT];
 #pragma unroll
@@ -106,7 +107,10 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
 #pragma unroll
         for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], ax[j], vout[j]);
       }
-      store_rpt<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout);
+      if (std::is_same<S, __nv_bfloat162>::value && p.salt)
+        store_rpt_sr<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout, srkey, uint32_t(boff + c * R));
+      else
+        store_rpt<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout);
       if (ACC == ACC_Y) {
         float2* yp = reinterpret_cast<float2*>(p.y) + boff + c * R;
 #pragma unroll

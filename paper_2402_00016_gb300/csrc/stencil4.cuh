@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
   const int r0 = lane * RPT;
   const bool bil_out = (p.flags & SF_BIL_OUT) != 0;
   const bool ef = (p.hint & 1) != 0;
+  const uint32_t srkey = sr_key(p);
   uint64_t pol = 0;
   if (ef) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   __shared__ double2 red[4][32];
@@ -307,7 +308,10 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
 #pragma unroll
         for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], ax[j], vout[j]);
       }
-      store_hint<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout, ef, pol);
+      if (std::is_same<S, __nv_bfloat162>::value && p.salt)
+        store_rpt_sr<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout, srkey, uint32_t(boff + c * R));
+      else
+        store_hint<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout, ef, pol);
       if (ACC == ACC_Y) {
         float2* yp = reinterpret_cast<float2*>(p.y) + boff + c * R;
 #pragma unroll

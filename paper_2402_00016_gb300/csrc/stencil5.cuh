@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(128, MINB) step5_kernel(step_params p, int n_c
   ring.spin = reinterpret_cast<S*>(smem + size_t(D) * SPP * 5 * sizeof(float4));
   const int lane = int(threadIdx.x) % L;
   const bool bil_out = (p.flags & SF_BIL_OUT) != 0;
+  const uint32_t srkey = sr_key(p);
   __shared__ double2 red[4][32];
   const int warp = threadIdx.x >> 5;
   const int wl = threadIdx.x & 31;
@@ -330,7 +331,10 @@ __global__ void __launch_bounds__(128, MINB) step5_kernel(step_params p, int n_c
       }
       {
         cx<T> o[1] = {vout};
-        store_rpt<S, 1>(reinterpret_cast<S*>(p.out) + boff + c * R, o);
+        if (std::is_same<S, __nv_bfloat162>::value && p.salt)
+          store_rpt_sr<S, 1>(reinterpret_cast<S*>(p.out) + boff + c * R, o, srkey, uint32_t(boff + c * R));
+        else
+          store_rpt<S, 1>(reinterpret_cast<S*>(p.out) + boff + c * R, o);
       }
       if (ACC == ACC_Y) {
         float2* yp = reinterpret_cast<float2*>(p.y) + boff + c * R;

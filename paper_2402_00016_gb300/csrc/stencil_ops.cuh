@@ -101,6 +101,58 @@ __device__ __forceinline__ void store_rpt(S* p, const cx<typename StoreTraits<S>
   }
 }
 
+// ------------------------------------------------------- stochastic rounding
+// 32 random bits for element `idx` of the rounding stream `key`: a 32-bit integer
+// hash (multiply-xorshift finaliser) of idx * golden-ratio constant + key.  The key
+// mixes a per-chain salt read from device memory with the step index, so the bits
+// are fresh for every element, step and chain application and do not depend on the
+// data being rounded.
+__device__ __forceinline__ uint32_t sr_bits(uint32_t idx, uint32_t key) {
+  uint32_t x = idx * 0x9E3779B1u + key;
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+// FP32 -> BF16 rounding the magnitude up with probability (discarded bits) / 2^16:
+// adding a uniform 16-bit r to the bit pattern carries into the kept half exactly
+// then, so E[result] = v (for finite v away from the overflow threshold).
+__device__ __forceinline__ uint32_t bf16_bits_sr(float v, uint32_t r16) {
+  const uint32_t u = __float_as_uint(v);
+  if ((u & 0x7f800000u) == 0x7f800000u) {  // Inf, NaN: as round to nearest
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    return uint32_t(*reinterpret_cast<const unsigned short*>(&b));
+  }
+  return (u + (r16 & 0xffffu)) >> 16;
+}
+
+// store_rpt with stochastic rounding of BF16 storage: element idx0 + j takes the random
+// bits sr_bits(idx0 + j, key) (FP32 and FP64 storage are stored exactly as store_rpt).
+template <typename S, int RPT>
+__device__ __forceinline__ void store_rpt_sr(S* p, const cx<typename StoreTraits<S>::R> (&v)[RPT], uint32_t key,
+                                             uint32_t idx0) {
+  if constexpr (std::is_same<S, __nv_bfloat162>::value) {
+    uint32_t w[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      const uint32_t r = sr_bits(idx0 + uint32_t(j), key);
+      w[j] = bf16_bits_sr(v[j].re, r) | (bf16_bits_sr(v[j].im, r >> 16) << 16);
+    }
+    if constexpr (RPT == 4) {
+      *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else if constexpr (RPT == 2) {
+      *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) reinterpret_cast<uint32_t*>(p)[j] = w[j];
+    }
+  } else {
+    store_rpt<S, RPT>(p, v);
+  }
+}
+
 // ------------------------------------------------------------ complex ops
 template <typename T>
 __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return cmake(a.re + b.re, a.im + b.im); }
@@ -271,5 +323,14 @@ __device__ __forceinline__ void hop_mu(const step_params& p, const S* base, int 
   fence<T, RPT>(acc);
 }
 
+}  // namespace sten
+}  // namespace mmc
+
+namespace mmc {
+namespace sten {
+// Key of the stochastic-rounding stream of one step launch (0 when rounding to nearest).
+__device__ __forceinline__ uint32_t sr_key(const step_params& p) {
+  return p.salt ? (__ldg(p.salt) ^ (uint32_t(p.step) * 0x85EBCA6Bu)) : 0u;
+}
 }  // namespace sten
 }  // namespace mmc

@@ -24,6 +24,7 @@ MMC_TAG_NOISE = 0x4E4F4953
 MMC_TAG_GMRES = 0x474D5253
 MMC_TAG_ARNOLDI = 0x4445464C
 MMC_NET_BASE = 0x100000
+MMC_ROUND_NEAREST, MMC_ROUND_STOCHASTIC = 0, 1
 MMC_NET_WEIGHTS = 1152
 PREC = {"f64": MMC_F64, "f32": MMC_F32, "bf16": MMC_BF16}
 THETA = {"1": MMC_THETA_ONE, "g4": MMC_THETA_G4, "g5": MMC_THETA_G5}
@@ -133,6 +134,9 @@ _SIGS = {
     "mmc_eig": (_i, [_i, _dp, _i, _dp, _dp]),
     "mmc_deflation_pairs": (_i, [_i, _dp, _dp, _d, _i, _ip, _ip, _ip]),
     "mmc_set_deflation_bound": (_i, [_vp, _d]),
+    "mmc_set_rounding": (_i, [_vp, _i, _u64]),
+    "mmc_net_set_precision": (_i, [_vp, _i, _i]),
+    "mmc_convert": (_i, [_vp, _vp, _i, _vp, _i, _i, _vp]),
     "mmc_gmres_poly_deflated": (_i, [_vp, _i, _i, _dp, _ip]),
     "mmc_probe_colouring": (_i, [_ip, _i, _ip, _ip]),
     "mmc_deflation_condition": (_i, [_i, _dp, _i, _ip, _d, _ip, _ip]),
@@ -573,3 +577,16 @@ def mmc_gmres_poly_deflated(ctx, m, op_handle=MMC_OP_M):
     h = ctypes.c_int()
     _check(lib.mmc_gmres_poly_deflated(ctx, int(m), int(op_handle), theta.ctypes.data_as(_dp), ctypes.byref(h)), ctx)
     return h.value, theta[0::2] + 1j * theta[1::2]
+
+
+def mmc_set_rounding(ctx, mode, seed=0):
+    """BF16 chain storage: MMC_ROUND_NEAREST or MMC_ROUND_STOCHASTIC (salt sequence from seed)."""
+    _check(lib.mmc_set_rounding(ctx, int(mode), int(seed) & 0xFFFFFFFFFFFFFFFF), ctx)
+
+
+def mmc_net_set_precision(ctx, handle, prec):
+    _check(lib.mmc_net_set_precision(ctx, int(handle), int(prec)), ctx)
+
+
+def mmc_convert(ctx, src, src_prec, dst, dst_prec, nrhs, stream=None):
+    _check(lib.mmc_convert(ctx, _ptr(src), int(src_prec), _ptr(dst), int(dst_prec), int(nrhs), _stream(stream)), ctx)

@@ -129,3 +129,60 @@ def test_level_and_exact_trace_with_network(mmc, env):
         got4 = mmc.mmc_trace_exact(ctx, h, mmc.MMC_THETA_G4, method)
         assert abs(got1 - ref1) < 1e-5 * abs(ref1)
         assert abs(got4 - ref4) < 1e-5 * abs(ref1)
+
+
+BF16_UNIT = 2.0 ** -8
+
+
+def test_bf16_network_forward_matches_oracle(mmc, env):
+    """BF16 weights and hidden activations, FP32 arithmetic: against the FP64 oracle with the
+    same (unrounded) weights.  Each weight and each stored hidden activation carries a
+    relative rounding error of at most 2^-9; through three layers of norm about 1 that
+    leaves a normwise relative error of a few times 2^-8: the bound is 4 x 2^-8."""
+    U, ctx = env
+    ws = learned.init_weights(3, scale=0.2)
+    h = mmc.mmc_net_create(ctx, ws)
+    mmc.mmc_net_set_precision(ctx, h, mmc.MMC_BF16)
+    B = 21
+    xin = _batch_canon(5, B)
+    x = mmc.new_field(ctx, B, mmc.MMC_F32)
+    y = mmc.new_field(ctx, B, mmc.MMC_F32)
+    mmc.mmc_pack(ctx, _to_rows(xin), B, mmc.MMC_F32, x)
+    xr = mmc.mmc_unpack(ctx, x, B, mmc.MMC_F32, 192)
+    mmc.mmc_net_apply(ctx, h, x, y, B)
+    got = mmc.mmc_unpack(ctx, y, B, mmc.MMC_F32, 192)
+    worst = 0.0
+    for j in range(B):
+        want = learned.forward(U, ws, xr[j].reshape(SHAPE)).ravel()
+        worst = max(worst, np.linalg.norm(got[j] - want) / np.linalg.norm(want))
+    assert worst < 4 * BF16_UNIT, worst
+    assert worst > 1e-5  # the BF16 path is really taken (FP32 gives ~1e-7)
+
+
+def test_bf16_network_gradients_and_training(mmc, env):
+    """Gradients of the BF16 forward pass against the oracle's FP64 gradients (bound 8 x 2^-8
+    normwise: the rounding of weights and stored activations enters the gradient through
+    both factors of every weight's sum), and BF16 training lowers the loss."""
+    U, ctx = env
+    ws = learned.init_weights(8, scale=0.2)
+    h = mmc.mmc_net_create(ctx, ws)
+    mmc.mmc_net_set_precision(ctx, h, mmc.MMC_BF16)
+    B = 16
+    e = _batch_canon(11, B)
+    t = _batch_canon(12, B)
+    ef = mmc.new_field(ctx, B, mmc.MMC_F32)
+    tf = mmc.new_field(ctx, B, mmc.MMC_F32)
+    mmc.mmc_pack(ctx, _to_rows(e), B, mmc.MMC_F32, ef)
+    mmc.mmc_pack(ctx, _to_rows(t), B, mmc.MMC_F32, tf)
+    e32 = mmc.mmc_unpack(ctx, ef, B, mmc.MMC_F32, 192).T.reshape(SHAPE + (B,))
+    t32 = mmc.mmc_unpack(ctx, tf, B, mmc.MMC_F32, 192).T.reshape(SHAPE + (B,))
+    L_ref, g_ref = learned.loss_and_grad(U, ws, e32, t32)
+    L, g = mmc.mmc_net_loss_grad(ctx, h, ef, tf, B)
+    assert abs(L - L_ref) < 8 * BF16_UNIT * abs(L_ref)
+    for G, Gr in zip(g, g_ref):
+        assert np.linalg.norm(G - Gr) < 8 * BF16_UNIT * np.linalg.norm(Gr)
+    h2 = mmc.mmc_net_create(ctx, None, 7)
+    mmc.mmc_net_set_precision(ctx, h2, mmc.MMC_BF16)
+    _, eta, xs = _solve_pairs(mmc, ctx, 64, 22)
+    hist = mmc.mmc_net_train(ctx, h2, eta, xs, 64, 16, 300, 3e-3)
+    assert hist[-10:].mean() < 0.5 * hist[:4].mean(), (hist[:4], hist[-10:])
