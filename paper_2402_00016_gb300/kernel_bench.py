@@ -35,6 +35,9 @@ def main(argv=None):
     ap.add_argument("--hint", type=int, default=-1, help="store hint of version 4 (1: L2 evict-first)")
     ap.add_argument("--sweep", default=None,
                     help="JSON list of variants {version, rpt, minb, spc, blocked, hint}: time each in turn")
+    ap.add_argument("--solve", type=int, default=0,
+                    help="m > 0: time nrhs refined solves (FGMRES(8)) right-preconditioned by a degree m-1 "
+                         "polynomial in Horner form (the step chains of the M^-1 level) instead of a level chain")
     ap.add_argument("--deflate", type=int, default=0,
                     help="k > 0: random deflation space of k vectors, levels deflated (tensor-core projections)")
     a = ap.parse_args(argv)
@@ -72,6 +75,22 @@ def main(argv=None):
         h = mmc.mmc_poly_from_roots(ctx, theta)
         h2 = mmc.mmc_poly_from_roots(ctx, theta[:2]) if a.deflate > 0 else mmc.MMC_ZERO
         defl = 1 if a.deflate > 0 else 0
+        if a.solve > 0:
+            hp = mmc.mmc_poly_from_roots(ctx, mmc.mmc_leja_order(
+                1.0 + 0.8 * np.exp(2j * np.pi * (np.arange(a.solve) + 0.5) / a.solve)))
+            b = mmc.new_field(ctx, a.nrhs, mmc.MMC_F64)
+            x = mmc.new_field(ctx, a.nrhs, mmc.MMC_F64)
+            mmc.mmc_noise(ctx, 2, 0, mmc.MMC_TAG_NOISE, a.nrhs, mmc.MMC_F64, b)
+            for rep in range(a.reps + 1):  # the first is the warm-up
+                if rep == 1:
+                    mmc.mmc_profile(ctx, 1)
+                x.zero_()
+                its, rel = mmc.mmc_solve(ctx, b, x, a.nrhs, 1e-8, hp, prec, 8, 400)
+            p = mmc.mmc_profile_read(ctx)
+            print(json.dumps({"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "solve_degree": a.solve - 1,
+                              "iterations": its, "step_launches": p["step_launches"],
+                              "classes": mmc.mmc_profile_classes(ctx)}), flush=True)
+            return
         variants = json.loads(a.sweep) if a.sweep else [None]
         vol = int(np.prod(a.dims))
         for var in variants:

@@ -212,3 +212,34 @@ def test_probing_equals_unit_sweep_8x4(mmc):
             assert abs(probe - unit) <= 1e-12 * scale, (th, probe, unit)
     finally:
         mmc.mmc_destroy(c)
+
+
+def test_deflated_double_polynomial_matches_oracle(mmc, small, ctx):
+    """The deflated double polynomial (reading of Sec. 7 / Sec. 9): the outer GMRES cycle
+    on phi_in(M) from the start vector without the deflated components gives the oracle's
+    harmonic Ritz values (1e-9, m_out = 4), and the deflated top level
+    Tr(M^-1 - p_dbl) samples with c_i = 1/lambda_i - p_dbl(lambda_i) match the oracle's
+    (dense inverse) within the solves' 1e-10 residual, with the exact correction to 1e-12."""
+    lam_o, Z_o, U_o, _ = small.eig[100.0]
+    mmc.mmc_set_deflation(ctx, lam_o, Z_o.T, U_o.T)
+    b = noise.z4_noise(DIMS, SEED, 0, 0, noise.TAG_GMRES).ravel()
+    t_in, t_out = deflation.deflated_double_poly_roots(small.op, b, 5, 4, Z_o, U_o)
+    h_in = mmc.mmc_poly_from_roots(ctx, t_in)
+    h_out, got_out = mmc.mmc_gmres_poly_deflated(ctx, 4, h_in)
+    assert np.abs(got_out - t_out).max() < 1e-9 * np.abs(t_out).max(), (got_out, t_out)
+    h_dbl = mmc.mmc_poly_double(ctx, h_in, mmc.mmc_poly_from_roots(ctx, t_out))
+    h_pre = mmc.mmc_poly_from_roots(ctx, small.th)
+    n = 5
+    st = mmc.mmc_trace_level(ctx, mmc.MMC_INV, h_dbl, mmc.MMC_THETA_ONE, 1, n, 0, 8, mmc.MMC_F64, precond=h_pre)
+    A = wilson.dense_M(small.U, KAPPA)
+    Ainv = np.linalg.inv(A)
+    c = 1.0 / lam_o - krylov.double_scalar(t_in, t_out, lam_o)
+    etas = [noise.z4_noise(DIMS, SEED, j, 8).ravel() for j in range(n)]
+    want, corr = estimator.level_samples(lambda v: Ainv @ v, lambda v: krylov.apply_double(small.op, t_in, t_out, v),
+                                         lambda v: v, etas, defl=(Z_o, U_o), c=c)
+    inv_norm = np.linalg.norm(Ainv, 2)
+    bound = small.n * inv_norm * 1.1e-10 + 1e-12 * np.abs(want).max()
+    assert st["k_deflated"] == len(lam_o)
+    assert np.abs(st["samples"] - want).max() <= bound, (np.abs(st["samples"] - want).max(), bound)
+    cscale = np.sum(np.abs(c) * np.linalg.norm(U_o, axis=0) * np.linalg.norm(Z_o, axis=0))
+    assert abs(st["corr_re"] + 1j * st["corr_im"] - corr) <= 1e-12 * cscale
