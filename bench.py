@@ -255,6 +255,9 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="the learned form: a BF16 network trained on 16^4 solve pairs as the M^-1 level's "
                          "preconditioner and as an extra level p_8 - N with Tr(N) exact")
+    ap.add_argument("--separate", dest="merged", action="store_false",
+                    help="run every polynomial level as its own chain (default: the polynomial levels in one "
+                         "batch, one launch per degree over all their chains)")
     ap.add_argument("--learned-pairs", type=int, default=4096)
     ap.add_argument("--learned-iters", type=int, default=1500)
     ap.add_argument("--cpu-reps", type=int, default=4, help="degree-2 oracle samples of the one-core leg")
@@ -367,12 +370,31 @@ def main():
         plan.append((h["p8"], h["net"], 0, 512, 5))
     samples_per_step = sum(n for (_, _, _, n, _) in plan)
 
+    nets = {h["net"]} if args.learned else set()
+
+    def batchable(hi, lo):
+        return hi != mmc.MMC_INV and hi not in nets and lo not in nets
+
     def step(it):
-        out = []
-        for (hi, lo, defl, n, lvl) in plan:
-            first = replicas.noise_first(it, rank, world, n)
-            out.append(mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, n, first, lvl, storage,
-                                           pre, want_samples=True))
+        out = [None] * len(plan)
+        if args.merged:
+            # the polynomial levels in one batch per deflation flag (one launch per degree
+            # over all their chains), the solve and network levels on their own
+            for defl in (0, 1):
+                idx = [i for i, (hi, lo, d, _, _) in enumerate(plan) if d == defl and batchable(hi, lo)]
+                if not idx:
+                    continue
+                res = mmc.mmc_trace_levels(ctx, [plan[i][0] for i in idx], [plan[i][1] for i in idx],
+                                           mmc.MMC_THETA_ONE, defl, [plan[i][3] for i in idx],
+                                           [replicas.noise_first(it, rank, world, plan[i][3]) for i in idx],
+                                           [plan[i][4] for i in idx], storage)
+                for i, r in zip(idx, res):
+                    out[i] = r
+        for i, (hi, lo, defl, n, lvl) in enumerate(plan):
+            if out[i] is None:
+                first = replicas.noise_first(it, rank, world, n)
+                out[i] = mmc.mmc_trace_level(ctx, hi, lo, mmc.MMC_THETA_ONE, defl, n, first, lvl, storage,
+                                             pre, want_samples=True)
         return out
 
     def barrier():
@@ -499,6 +521,7 @@ def main():
                    "levels": LEVELS + (["p_8 - N (learned)"] if args.learned else []), "double": {"m_in": 40, "m_out": args.outer_m, "deflated": args.dbl_deflated},
                    "noises": [n for (_, _, _, n, _) in plan], "storage": args.storage, "rounding": args.rounding, "arithmetic": "fp32, fp64 bilinears",
                    "deflated": len(lam), "probe_colours": ncol,
+                   "batch": "polynomial levels merged (one launch per degree)" if args.merged else "per level",
                    "solves": {"fgmres_m": args.solve_m, "precond": "p_in (degree 39)" if args.precond == "in"
                               else "p_dbl (degree 319)", "tol": 1e-10, "inner_storage": args.solve_storage}, "l2": "inputs larger than L2 (GB-sized fields)",
                    "parallelism": "replicas" if world > 1 else "1 gpu"},
@@ -548,6 +571,11 @@ def main():
     line["estimate"]["time_x_var"] = t_opt * var_over_n
     line["estimate"]["eps_target"] = eps_target
     line["estimate"]["seconds_to_eps"] = t_opt * var_over_n / eps_target ** 2
+    # with the noise counts re-allocated cost-optimally (the cost function Sec. 9 names:
+    # N_l proportional to sqrt(V_l / C_l), C_l the measured seconds per sample) the time to
+    # eps is (sum_l sqrt(V_l C_l))^2 / eps^2
+    sv = sum(np.sqrt(max(r["var_re"], 0.0) * r["seconds"] / n) for r, (_, _, _, n, _) in zip(last, plan))
+    line["estimate"]["seconds_to_eps_cost_optimal"] = sv ** 2 / eps_target ** 2
     if plain:
         t_plain = sum(n * t for (_, _, _, n, _), t in zip(plan, plain["seconds_per_sample_by_level"]))
         plain["time_x_var"] = t_plain * var_over_n

@@ -264,6 +264,26 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
                     uint32_t first_noise, uint32_t level, int prec, int precond,
                     mmc_level_stats* out, double* samples_out);
 
+/* n_levels polynomial levels in one batch (Eq. 2, Sec. 6; the multilevel batch of
+ * Sec. 7 and Sec. 8, whose levels have uneven noise counts and degrees): level l has
+ * operands hi[l] (polynomial handle) and lo[l] (polynomial handle or MMC_ZERO),
+ * n_noise[l] Z(4) vectors with noise indices first_noise[l].. of level id level[l].
+ * Each operand gets its own slot of rhs blocks holding its level's noise, and every
+ * single polynomial in M of degree >= 1 runs in one step chain over all slots: one
+ * launch per degree up to the highest, each rhs block stopping after its own
+ * polynomial's degree.  Double polynomials and degree-0 operands run on their slots
+ * afterwards.  Samples, deflation (deflate != 0) and statistics are exactly those of
+ * mmc_trace_level on the same noises (up to the summation order of the bilinears);
+ * out[l].seconds is the level's share of the batch's time (the shared chain by rhs
+ * steps, the noise by slots) plus its own double-polynomial and deflation time.
+ * samples_out (may be NULL) holds n_levels pointers, each NULL or to 2 n_noise[l]
+ * doubles.  Device memory: three fields of sum_l (slots of level l) rhs.  Errors:
+ * MMC_ERR_ARG for MMC_INV or network operands (use mmc_trace_level), counts < 1 or
+ * other bad arguments; those of mmc_trace_level. */
+int mmc_trace_levels(mmc_ctx* ctx, int n_levels, const int* hi, const int* lo, const int* n_noise,
+                     const uint32_t* first_noise, const uint32_t* level, int theta_op, int deflate, int prec,
+                     mmc_level_stats* out, double* const* samples_out);
+
 /* One level of a multilevel estimate (see mmc_estimate). */
 typedef struct {
   int hi, lo;          /* level operands, as in mmc_trace_level */
@@ -452,7 +472,8 @@ int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters);
  * warp, for Lx * R up to 384, falling back to 2 otherwise; 4: as 2 with one
  * rhs per lane, a persistent grid whose CTAs take (rhs block, pass of sites)
  * items round-robin so that the sites in flight form one compact front, and
- * the loads of each hop issued while the previous hop computes; 5: as 4 with
+ * the loads of each hop issued while the previous hop computes (minb 3: 168
+ * registers, 4: 128, 5: 128 with each pass's links staged in shared memory); 5: as 4 with
  * the operands of the hops staged in shared memory by per-lane asynchronous
  * copies several hops ahead, the depth set by 300 + n, FP32 3 or 4 (default 4),
  * BF16 4 (default) or 6), or 200 + b

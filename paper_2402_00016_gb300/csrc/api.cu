@@ -488,9 +488,10 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
         bo = ordr;
       }
     }
-    // the persistent, pipelined form (version 4, one rhs per lane): register caps and traversals
+    // the persistent, pipelined form (version 4, one rhs per lane): register caps (3: 168
+    // registers, 4: 128, 5: 128 with the links staged in shared memory) and traversals
     for (int ordr = 0; ordr <= 2; ++ordr)
-    for (int mb = 3; mb <= 4; ++mb) {
+    for (int mb = 3; mb <= 5; ++mb) {
       if ((ordr == 1 && !ctx->order) || (ordr == 2 && !ctx->order_zh)) continue;
       ctx->var_ver[prec][rc] = 4;
       ctx->var_rpt[prec][rc] = 1;

@@ -225,7 +225,8 @@ struct Run {
   int theta = 0;
   double2* partial = nullptr;     // [nbx][npad]
   int nbx = 0;
-  const int* rb_len = nullptr;
+  const int* rb_len = nullptr;     // device: steps per rhs block (blocks with step >= len skip)
+  std::vector<int> rb_len_host;   // the same on the host (launch accounting)
   bool dagger = false;
   std::vector<Step> steps;
 };
@@ -281,12 +282,16 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
   for (size_t k = 0; k < run.steps.size(); ++k)
     for (size_t i = 0; i < per; ++i)
       host[k * per + i] = make_double2(run.steps[k].coef[i].real(), run.steps[k].coef[i].imag());
-  // FNV-1a hash of the table (and its size) as the cache key
+  // hash of the table (and its size) as the cache key: FNV-1a over 64-bit words, with
+  // the high half folded in after each multiply
   uint64_t key = 1469598103934665603ull ^ host.size();
   {
-    const unsigned char* b = reinterpret_cast<const unsigned char*>(host.data());
-    const size_t nb = host.size() * sizeof(double2);
-    for (size_t i = 0; i < nb; ++i) key = (key ^ b[i]) * 1099511628211ull;
+    const uint64_t* w = reinterpret_cast<const uint64_t*>(host.data());
+    const size_t nw = host.size() * sizeof(double2) / sizeof(uint64_t);
+    for (size_t i = 0; i < nw; ++i) {
+      key = (key ^ w[i]) * 1099511628211ull;
+      key ^= key >> 29;
+    }
   }
   void* dcoef = nullptr;
   auto hit = ctx->coef_cache.find(key);
@@ -402,7 +407,8 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       }
       if (!done && ver_run == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e4 = cudaSuccess;
-        const int mb = ctx->var_minb[run.prec][rc] == 3 ? 3 : 4;
+        const int mbr = ctx->var_minb[run.prec][rc];
+        const int mb = mbr == 3 ? 3 : (mbr == 5 ? 5 : 4);
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
         done = run.prec == MMC_F32 ? mmc::launch_step4_f32(g.R, mb, p, g.nrb, nbx, s, &e4)
                                    : mmc::launch_step4_bf16(g.R, mb, p, g.nrb, nbx, s, &e4);
@@ -515,6 +521,12 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
   if (!cgp) TRY(launch_steps(prof, s));
   for (size_t k = 0; k < run.steps.size(); ++k) {
     const Step& st = run.steps[k];
+    // rhs of the launch's active blocks (all of them without per-block chain lengths)
+    int active = g.npad;
+    if (!run.rb_len_host.empty()) {
+      active = 0;
+      for (int len : run.rb_len_host) active += (int(k) < len) ? g.R : 0;
+    }
     if (prof) {
       ctx->prof_launches += 1;
       // algorithmic bytes and flops of this launch (all rhs blocks active), the bytes
@@ -529,8 +541,8 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
                              ((st.flags & mmc::SF_YACC) ? 2.0 * 12 * (run.prec == MMC_F64 ? 16 : 8) : 0.0) +
                              ((st.flags & mmc::SF_BIL_LEFT) ? sb : 0.0);
       const double links = (st.flags & mmc::SF_HOP) ? 4.0 * 9 * (run.prec == MMC_F64 ? 16 : 8) : 0.0;
-      const double bytes = double(ctx->V) * (double(g.npad) * per_rhs + links);
-      const double flops = double(ctx->V) * g.npad * (((st.flags & mmc::SF_HOP) ? 1368.0 : 0.0) + 48.0);
+      const double bytes = active ? double(ctx->V) * (double(active) * per_rhs + links) : 0.0;
+      const double flops = double(ctx->V) * active * (((st.flags & mmc::SF_HOP) ? 1368.0 : 0.0) + 48.0);
       ctx->prof_bytes += bytes;
       ctx->prof_flops += flops;
       mmc_profile_class& pc = ctx->prof_classes[cls];
@@ -538,7 +550,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       pc.bytes += bytes;
       pc.flops += flops;
     }
-    if (st.flags & mmc::SF_HOP) ctx->matvecs += g.npad;
+    if (st.flags & mmc::SF_HOP) ctx->matvecs += active;
   }
   return MMC_OK;
 }

@@ -554,6 +554,142 @@ int mmc_solve(mmc_ctx* ctx, const void* b, void* x, int nrhs, double rel_tol, in
   return rc;
 }
 
+namespace {
+
+// Deflation correction and statistics of one level whose raw samples x[r] (r < n_noise)
+// are formed: subtracts sum_i c_i (eta^H Theta z_i)(u_i^H eta) with c_i the level's
+// scalar function at lambda_i and reports the exact correction sum_i c_i u_i^H Theta z_i
+// (Sec. 7); mean, unbiased variances and standard errors (Sec. 4, Sec. 8).  g and codes
+// describe the level's noise (rhs blocks of g.R, codes [rb][site][g.R]); `seconds` is
+// the time already spent on the level, this call's own time is added.
+int finish_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int n_noise, const geom& g,
+                 const uint32_t* codes, int prec, std::vector<cd>& x, long long matvecs, double seconds,
+                 mmc_level_stats* out, double* samples_out, cudaStream_t s) {
+  const auto t1 = std::chrono::steady_clock::now();
+  void* part;
+  TRY(scratch(ctx, "lv_fpart", size_t((g.V + kSpc - 1) / kSpc) * std::max(g.npad, 1) * sizeof(double2), &part));
+  cd corr(0, 0);
+  int kd = 0;
+  if (deflate && ctx->k_defl > 0) {
+    const int k = ctx->k_defl;
+    kd = k;
+    const geom g1 = make_geom(ctx, 1);
+    const int nb2 = (g.V + kSpc - 1) / kSpc;
+    void *pa, *pb;
+    TRY(scratch(ctx, "lv_pa", size_t(nb2) * k * g.npad * sizeof(double2), &pa));
+    TRY(scratch(ctx, "lv_pb", size_t(nb2) * k * g.npad * sizeof(double2), &pb));
+    const size_t n = size_t(ctx->V) * 12;
+    std::vector<cd> A, B, D(k);
+    if (prec != MMC_F64 && ctx->use_tc && k <= 128) {
+      // tensor cores: one BF16 GEMM for both projections; the correction from the same BF16 copy
+      const long long Kp = ((24ll * ctx->V + 63) / 64) * 64;
+      if (!ctx->tcB[theta_op]) {
+        CK(cudaMalloc(&ctx->tcB[theta_op], size_t(256) * Kp * 2));
+        CK(mmc::launch_tc_pack_eig(ctx->V, k, Kp, theta_op, ctx->Z32, ctx->U32, ctx->tcB[theta_op], s));
+      }
+      const int mtiles = (2 * g.npad + 127) / 128;
+      int nsplit = std::max(1, 148 / mtiles);
+      nsplit = int(std::min<long long>(nsplit, Kp / 64));
+      void *tpart, *tP, *terr, *tdots;
+      TRY(scratch(ctx, "tc_part", size_t(nsplit) * mtiles * 128 * 256 * sizeof(float), &tpart));
+      TRY(scratch(ctx, "tc_P", size_t(mtiles) * 128 * 256 * sizeof(double), &tP));
+      TRY(scratch(ctx, "tc_err", sizeof(int), &terr));
+      TRY(scratch(ctx, "tc_dots", size_t(k) * sizeof(double2), &tdots));
+      CK(cudaMemsetAsync(terr, 0, sizeof(int), s));
+      CK(mmc::launch_tc_proj(g, (const uint32_t*)codes, ctx->tcB[theta_op], Kp, nsplit, (float*)tpart, (double*)tP,
+                             (int*)terr, s));
+      // the exact correction's dots depend on the deflation data only: computed once per Theta
+      const bool new_dots = ctx->tc_dots[theta_op].size() != size_t(k);
+      if (new_dots) CK(mmc::launch_tc_pair_dots(Kp, k, ctx->tcB[theta_op], (double2*)tdots, s));
+      std::vector<double> P(size_t(mtiles) * 128 * 256);
+      std::vector<double2> dd(k);
+      int herr = 0;
+      CK(cudaMemcpyAsync(P.data(), tP, P.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (new_dots) CK(cudaMemcpyAsync(dd.data(), tdots, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (herr) RET(MMC_ERR_TIMEOUT, "mmc_trace_level: tensor-core projection wait timed out");
+      A.assign(size_t(k) * g.npad, cd(0, 0));
+      B.assign(size_t(k) * g.npad, cd(0, 0));
+      for (int i = 0; i < k; ++i)
+        for (int r = 0; r < g.npad; ++r) {
+          const double* row0 = &P[size_t(2 * r) * 256];
+          const double* row1 = &P[size_t(2 * r + 1) * 256];
+          A[size_t(i) * g.npad + r] = cd(row0[i], -row1[i]);
+          B[size_t(i) * g.npad + r] = cd(row0[128 + i], row1[128 + i]);
+        }
+      if (new_dots) {
+        ctx->tc_dots[theta_op].resize(k);
+        for (int i = 0; i < k; ++i) ctx->tc_dots[theta_op][i] = cd(dd[i].x, dd[i].y);
+      }
+      D = ctx->tc_dots[theta_op];
+    } else {
+      const int dp = prec == MMC_F64 ? MMC_F64 : MMC_F32;  // eigenvector copy matching the level's precision
+      const void* Zd = dp == MMC_F64 ? (const void*)ctx->Z : (const void*)ctx->Z32;
+      const void* Ud = dp == MMC_F64 ? (const void*)ctx->U : (const void*)ctx->U32;
+      CK(mmc::launch_defl_proj(dp, g, (const uint32_t*)codes, theta_op, Zd, Ud, k, kSpc, (double2*)pa, (double2*)pb,
+                               s));
+      TRY(reduce_to_host(ctx, (double2*)pa, nb2, k, g.npad, A, s));
+      TRY(reduce_to_host(ctx, (double2*)pb, nb2, k, g.npad, B, s));
+      for (int i = 0; i < k; ++i) {
+        const void* ui =
+            dp == MMC_F64 ? (const void*)(ctx->U + size_t(i) * n) : (const void*)(ctx->U32 + size_t(i) * n);
+        const void* zi =
+            dp == MMC_F64 ? (const void*)(ctx->Z + size_t(i) * n) : (const void*)(ctx->Z32 + size_t(i) * n);
+        CK(mmc::launch_multidot(dp, g1, ui, 0, 1, zi, theta_op, kSpc, (double2*)part, s));
+        std::vector<cd> d;
+        TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, 1, d, s));
+        D[i] = d[0];
+      }
+    }
+    for (int i = 0; i < k; ++i) {
+      // c_i: the level's scalar function at lambda_i (1/lambda_i for M^-1)
+      const cd fhi = hi == MMC_INV ? 1.0 / ctx->lambda[i] : poly_value(ctx, hi, ctx->lambda[i]);
+      cd c = fhi - (lo == MMC_ZERO ? cd(0, 0) : poly_value(ctx, lo, ctx->lambda[i]));
+      for (int r = 0; r < n_noise; ++r) x[r] -= c * A[size_t(i) * g.npad + r] * B[size_t(i) * g.npad + r];
+      corr += c * D[i];
+    }
+  }
+  // statistics (Sec. 4, Sec. 8 readings: unbiased variance of each part, stderr = s / sqrt(N))
+  cd mean(0, 0);
+  for (int r = 0; r < n_noise; ++r) mean += x[r];
+  mean /= double(n_noise);
+  double vr = 0, vi = 0, cv = 0;
+  for (int r = 0; r < n_noise; ++r) {
+    cd d = x[r] - mean;
+    vr += d.real() * d.real();
+    vi += d.imag() * d.imag();
+    cv += std::norm(d);
+  }
+  const double dn = n_noise > 1 ? double(n_noise - 1) : 1.0;
+  std::memset(out, 0, sizeof(*out));
+  out->n = n_noise;
+  out->k_deflated = kd;
+  out->mean_re = mean.real();
+  out->mean_im = mean.imag();
+  out->var_re = n_noise > 1 ? vr / dn : 0.0;
+  out->var_im = n_noise > 1 ? vi / dn : 0.0;
+  out->cvar = n_noise > 1 ? cv / dn : 0.0;
+  out->stderr_re = std::sqrt(out->var_re / n_noise);
+  out->stderr_im = std::sqrt(out->var_im / n_noise);
+  out->corr_re = corr.real();
+  out->corr_im = corr.imag();
+  out->value_re = mean.real() + corr.real();
+  out->value_im = mean.imag() + corr.imag();
+  out->matvecs = matvecs;
+  out->seconds = seconds + std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+  if (samples_out)
+    for (int r = 0; r < n_noise; ++r) {
+      samples_out[2 * r] = x[r].real();
+      samples_out[2 * r + 1] = x[r].imag();
+    }
+  for (int r = 0; r < n_noise; ++r)
+    if (!std::isfinite(x[r].real()) || !std::isfinite(x[r].imag())) RET(MMC_ERR_NAN, "mmc_trace_level: NaN sample");
+  return MMC_OK;
+}
+
+}  // namespace
+
 int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int n_noise, uint32_t first,
                     uint32_t level, int prec, int precond, mmc_level_stats* out, double* samples_out) {
   TRY(check_ctx(ctx));
@@ -673,123 +809,191 @@ int mmc_trace_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int
     TRY(poly_bilinear(hi, 1.0));
   }
   if (lo != MMC_ZERO && hi != MMC_INV) TRY(poly_bilinear(lo, -1.0));
-  cd corr(0, 0);
-  int kd = 0;
-  if (deflate && ctx->k_defl > 0) {
-    const int k = ctx->k_defl;
-    kd = k;
-    const geom g1 = make_geom(ctx, 1);
-    const int nb2 = (g.V + kSpc - 1) / kSpc;
-    void *pa, *pb;
-    TRY(scratch(ctx, "lv_pa", size_t(nb2) * k * g.npad * sizeof(double2), &pa));
-    TRY(scratch(ctx, "lv_pb", size_t(nb2) * k * g.npad * sizeof(double2), &pb));
-    const size_t n = size_t(ctx->V) * 12;
-    std::vector<cd> A, B, D(k);
-    if (prec != MMC_F64 && ctx->use_tc && k <= 128) {
-      // tensor cores: one BF16 GEMM for both projections; the correction from the same BF16 copy
-      const long long Kp = ((24ll * ctx->V + 63) / 64) * 64;
-      if (!ctx->tcB[theta_op]) {
-        CK(cudaMalloc(&ctx->tcB[theta_op], size_t(256) * Kp * 2));
-        CK(mmc::launch_tc_pack_eig(ctx->V, k, Kp, theta_op, ctx->Z32, ctx->U32, ctx->tcB[theta_op], s));
-      }
-      const int mtiles = (2 * g.npad + 127) / 128;
-      int nsplit = std::max(1, 148 / mtiles);
-      nsplit = int(std::min<long long>(nsplit, Kp / 64));
-      void *tpart, *tP, *terr, *tdots;
-      TRY(scratch(ctx, "tc_part", size_t(nsplit) * mtiles * 128 * 256 * sizeof(float), &tpart));
-      TRY(scratch(ctx, "tc_P", size_t(mtiles) * 128 * 256 * sizeof(double), &tP));
-      TRY(scratch(ctx, "tc_err", sizeof(int), &terr));
-      TRY(scratch(ctx, "tc_dots", size_t(k) * sizeof(double2), &tdots));
-      CK(cudaMemsetAsync(terr, 0, sizeof(int), s));
-      CK(mmc::launch_tc_proj(g, (const uint32_t*)codes, ctx->tcB[theta_op], Kp, nsplit, (float*)tpart, (double*)tP,
-                             (int*)terr, s));
-      // the exact correction's dots depend on the deflation data only: computed once per Theta
-      const bool new_dots = ctx->tc_dots[theta_op].size() != size_t(k);
-      if (new_dots) CK(mmc::launch_tc_pair_dots(Kp, k, ctx->tcB[theta_op], (double2*)tdots, s));
-      std::vector<double> P(size_t(mtiles) * 128 * 256);
-      std::vector<double2> dd(k);
-      int herr = 0;
-      CK(cudaMemcpyAsync(P.data(), tP, P.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-      if (new_dots) CK(cudaMemcpyAsync(dd.data(), tdots, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (herr) RET(MMC_ERR_TIMEOUT, "mmc_trace_level: tensor-core projection wait timed out");
-      A.assign(size_t(k) * g.npad, cd(0, 0));
-      B.assign(size_t(k) * g.npad, cd(0, 0));
-      for (int i = 0; i < k; ++i)
-        for (int r = 0; r < g.npad; ++r) {
-          const double* row0 = &P[size_t(2 * r) * 256];
-          const double* row1 = &P[size_t(2 * r + 1) * 256];
-          A[size_t(i) * g.npad + r] = cd(row0[i], -row1[i]);
-          B[size_t(i) * g.npad + r] = cd(row0[128 + i], row1[128 + i]);
-        }
-      if (new_dots) {
-        ctx->tc_dots[theta_op].resize(k);
-        for (int i = 0; i < k; ++i) ctx->tc_dots[theta_op][i] = cd(dd[i].x, dd[i].y);
-      }
-      D = ctx->tc_dots[theta_op];
-    } else {
-      const int dp = prec == MMC_F64 ? MMC_F64 : MMC_F32;  // eigenvector copy matching the level's precision
-      const void* Zd = dp == MMC_F64 ? (const void*)ctx->Z : (const void*)ctx->Z32;
-      const void* Ud = dp == MMC_F64 ? (const void*)ctx->U : (const void*)ctx->U32;
-      CK(mmc::launch_defl_proj(dp, g, (const uint32_t*)codes, theta_op, Zd, Ud, k, kSpc, (double2*)pa, (double2*)pb,
-                               s));
-      TRY(reduce_to_host(ctx, (double2*)pa, nb2, k, g.npad, A, s));
-      TRY(reduce_to_host(ctx, (double2*)pb, nb2, k, g.npad, B, s));
-      for (int i = 0; i < k; ++i) {
-        const void* ui =
-            dp == MMC_F64 ? (const void*)(ctx->U + size_t(i) * n) : (const void*)(ctx->U32 + size_t(i) * n);
-        const void* zi =
-            dp == MMC_F64 ? (const void*)(ctx->Z + size_t(i) * n) : (const void*)(ctx->Z32 + size_t(i) * n);
-        CK(mmc::launch_multidot(dp, g1, ui, 0, 1, zi, theta_op, kSpc, (double2*)part, s));
-        std::vector<cd> d;
-        TRY(reduce_to_host(ctx, (double2*)part, nb2, 1, 1, d, s));
-        D[i] = d[0];
-      }
-    }
-    for (int i = 0; i < k; ++i) {
-      // c_i: the level's scalar function at lambda_i (1/lambda_i for M^-1)
-      const cd fhi = hi == MMC_INV ? 1.0 / ctx->lambda[i] : poly_value(ctx, hi, ctx->lambda[i]);
-      cd c = fhi - (lo == MMC_ZERO ? cd(0, 0) : poly_value(ctx, lo, ctx->lambda[i]));
-      for (int r = 0; r < n_noise; ++r) x[r] -= c * A[size_t(i) * g.npad + r] * B[size_t(i) * g.npad + r];
-      corr += c * D[i];
-    }
+  return finish_level(ctx, hi, lo, theta_op, deflate, n_noise, g, (const uint32_t*)codes, prec, x,
+                      ctx->matvecs - mv0,
+                      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), out,
+                      samples_out, s);
+}
+
+// Several polynomial levels in one batch.  Every level's hi and lo operand gets its own
+// slot of rhs blocks (its noise repeated), and all single polynomials in M (Leja
+// products, Sec. 3) run as one step chain: one launch per degree over the slots of
+// every chain still running (per-block chain lengths), so the uneven noise counts
+// and degrees of the levels share launches.  Double polynomials (Sec. 5) and
+// degree-0 operands run on their own slots afterwards.  Samples, deflation and
+// statistics are those of mmc_trace_level on the same noises.
+int mmc_trace_levels(mmc_ctx* ctx, int n_levels, const int* hi, const int* lo, const int* n_noise,
+                     const uint32_t* first, const uint32_t* level, int theta_op, int deflate, int prec,
+                     mmc_level_stats* out, double* const* samples_out) {
+  TRY(check_ctx(ctx));
+  if (n_levels < 1 || !hi || !lo || !n_noise || !first || !level || !out || prec < 0 || prec > 2 || theta_op < 0 ||
+      theta_op > 2)
+    RET(MMC_ERR_ARG, "mmc_trace_levels: bad argument");
+  for (int l = 0; l < n_levels; ++l) {
+    if (n_noise[l] < 1) RET(MMC_ERR_ARG, "mmc_trace_levels: a level has no noise");
+    if (!valid_poly(ctx, hi[l]) || !(lo[l] == MMC_ZERO || valid_poly(ctx, lo[l])))
+      RET(MMC_ERR_ARG, "mmc_trace_levels: level operands must be polynomial handles (lo may be MMC_ZERO); "
+                       "solve and network levels run through mmc_trace_level");
+    for (int h : {hi[l], lo[l]})
+      if (h != MMC_ZERO && ctx->polys[h].kind == 0 && ctx->polys[h].op != MMC_OP_M)
+        RET(MMC_ERR_ARG, "mmc_trace_levels: polynomial in phi_h is not applicable alone");
   }
-  // statistics (Sec. 4, Sec. 8 readings: unbiased variance of each part, stderr = s / sqrt(N))
-  cd mean(0, 0);
-  for (int r = 0; r < n_noise; ++r) mean += x[r];
-  mean /= double(n_noise);
-  double vr = 0, vi = 0, cv = 0;
-  for (int r = 0; r < n_noise; ++r) {
-    cd d = x[r] - mean;
-    vr += d.real() * d.real();
-    vi += d.imag() * d.imag();
-    cv += std::norm(d);
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = ctx->stream;
+  struct Chain {
+    int l, h;
+    double sign;
+    bool merged;
+    int r0, slot;  // first rhs and padded rhs count of the chain's slot
+  };
+  std::vector<Chain> ch;
+  long long nsum = 0;
+  for (int pass = 0; pass < 2; ++pass)  // the merged chains first: their slots form a prefix
+    for (int l = 0; l < n_levels; ++l)
+      for (int side = 0; side < 2; ++side) {
+        const int h = side == 0 ? hi[l] : lo[l];
+        if (h == MMC_ZERO) continue;
+        const Poly& P = ctx->polys[h];
+        const bool merged = P.kind == 0 && P.theta.size() >= 2;
+        if (merged != (pass == 0)) continue;
+        ch.push_back({l, h, side == 0 ? 1.0 : -1.0, merged, 0, 0});
+        nsum += n_noise[l];
+      }
+  if (nsum > (1ll << 24)) RET(MMC_ERR_ARG, "mmc_trace_levels: too many noise vectors in one batch");
+  const int R = rhs_block(int(nsum), ctx->rhs_max);
+  int npad_m = 0, npad_a = 0;
+  for (Chain& c : ch) {
+    c.slot = (n_noise[c.l] + R - 1) / R * R;
+    c.r0 = npad_a;
+    npad_a += c.slot;
+    if (c.merged) npad_m = npad_a;
   }
-  const double dn = n_noise > 1 ? double(n_noise - 1) : 1.0;
-  std::memset(out, 0, sizeof(*out));
-  out->n = n_noise;
-  out->k_deflated = kd;
-  out->mean_re = mean.real();
-  out->mean_im = mean.imag();
-  out->var_re = n_noise > 1 ? vr / dn : 0.0;
-  out->var_im = n_noise > 1 ? vi / dn : 0.0;
-  out->cvar = n_noise > 1 ? cv / dn : 0.0;
-  out->stderr_re = std::sqrt(out->var_re / n_noise);
-  out->stderr_im = std::sqrt(out->var_im / n_noise);
-  out->corr_re = corr.real();
-  out->corr_im = corr.imag();
-  out->value_re = mean.real() + corr.real();
-  out->value_im = mean.imag() + corr.imag();
-  out->matvecs = ctx->matvecs - mv0;
-  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (samples_out)
-    for (int r = 0; r < n_noise; ++r) {
-      samples_out[2 * r] = x[r].real();
-      samples_out[2 * r + 1] = x[r].imag();
+  auto geom_of = [&](int npad) {
+    geom g;
+    g.V = ctx->V;
+    g.R = R;
+    g.nrb = npad / R;
+    g.npad = npad;
+    return g;
+  };
+  const geom ga = geom_of(npad_a);
+  const int nbx = nbx_step(ctx);
+  void *codes, *X, *part, *dids;
+  TRY(scratch(ctx, "lv_codes", size_t(npad_a) * ga.V * sizeof(uint32_t), &codes));
+  TRY(scratch(ctx, "lv_X", field_bytes(ga, prec), &X));
+  TRY(scratch(ctx, "lv_part", size_t(std::max(nbx, (ga.V + kSpc - 1) / kSpc)) * npad_a * sizeof(double2), &part));
+  std::vector<uint2> ids(npad_a);
+  for (const Chain& c : ch)
+    for (int j = 0; j < c.slot; ++j)
+      ids[c.r0 + j] = j < n_noise[c.l] ? make_uint2(level[c.l], first[c.l] + j) : make_uint2(0xffffffffu, 0);
+  TRY(scratch(ctx, "lv_ids", ids.size() * sizeof(uint2), &dids));
+  CK(cudaMemcpyAsync(dids, ids.data(), ids.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+  CK(mmc::launch_noise(prec, ga, (const uint2*)dids, MMC_TAG_NOISE, ctx->seed, X, (uint32_t*)codes, s));
+
+  std::vector<std::vector<cd>> x(n_levels);
+  std::vector<double> secs(n_levels, 0.0);
+  std::vector<long long> mvs(n_levels, 0);
+  for (int l = 0; l < n_levels; ++l) x[l].assign(size_t(n_noise[l]), cd(0, 0));
+  const size_t elem = elem_bytes(prec);
+  if (npad_m > 0) {
+    const geom gm = geom_of(npad_m);
+    void *P0, *P1, *dlen;
+    TRY(scratch(ctx, "P0", field_bytes(gm, prec), &P0));
+    TRY(scratch(ctx, "P1", field_bytes(gm, prec), &P1));
+    Run run;
+    run.g = gm;
+    run.prec = prec;
+    run.codes = (const uint32_t*)codes;
+    run.theta = theta_op;
+    run.partial = (double2*)part;
+    run.nbx = nbx;
+    run.rb_len_host.assign(gm.nrb, 0);
+    int steps = 0;
+    for (const Chain& c : ch)
+      if (c.merged) {
+        const int len = int(ctx->polys[c.h].theta.size()) - 1;
+        for (int b = c.r0 / R; b < (c.r0 + c.slot) / R; ++b) run.rb_len_host[b] = len;
+        steps = std::max(steps, len);
+      }
+    TRY(scratch(ctx, "lv_rblen", size_t(gm.nrb) * sizeof(int), &dlen));
+    CK(cudaMemcpyAsync(dlen, run.rb_len_host.data(), size_t(gm.nrb) * sizeof(int), cudaMemcpyHostToDevice, s));
+    run.rb_len = (const int*)dlen;
+    const double kap = ctx->kappa;
+    void* P[2] = {P0, P1};
+    for (int k = 0; k < steps; ++k) {
+      // step k of every chain still running: prod_{k+1} = (1 - M/theta_k) prod_k, the
+      // bilinear taking (1/theta_k) eta^H Theta prod_k and, on a chain's last step, its
+      // last term (1/theta_m) eta^H Theta prod_m from the output (build_single's program)
+      Step st;
+      st.in = (k == 0) ? X : P[(k - 1) & 1];
+      st.out = P[k & 1];
+      st.flags = mmc::SF_HOP | mmc::SF_WRITE | mmc::SF_BIL_CODES;
+      st.coef = coef_block(npad_m);
+      for (const Chain& c : ch) {
+        if (!c.merged) continue;
+        const std::vector<cd>& th = ctx->polys[c.h].theta;
+        const int m = int(th.size());
+        if (k >= m - 1) continue;
+        const cd it = 1.0 / th[k];
+        const cd wo = (k == m - 2) ? 1.0 / th[m - 1] : cd(0, 0);
+        if (k == m - 2) st.flags |= mmc::SF_BIL_OUT;
+        for (int j = 0; j < n_noise[c.l]; ++j) set_coef(st.coef, npad_m, c.r0 + j, 1.0 - it, kap * it, 0, it, wo);
+      }
+      run.steps.push_back(st);
     }
-  for (int r = 0; r < n_noise; ++r)
-    if (!std::isfinite(x[r].real()) || !std::isfinite(x[r].imag())) RET(MMC_ERR_NAN, "mmc_trace_level: NaN sample");
+    CK(cudaMemsetAsync(part, 0, size_t(nbx) * npad_m * sizeof(double2), s));
+    const auto tm = std::chrono::steady_clock::now();
+    TRY(exec_run(ctx, run, s));
+    std::vector<cd> v;
+    TRY(reduce_to_host(ctx, (double2*)part, nbx, 1, npad_m, v, s));
+    // chain time shared by the levels in proportion to their rhs steps; the noise to all
+    // levels in proportion to their slots
+    const double t_chain = std::chrono::duration<double>(std::chrono::steady_clock::now() - tm).count();
+    const double t_noise = std::chrono::duration<double>(tm - t0).count();
+    double work = 0;
+    for (const Chain& c : ch)
+      if (c.merged) work += double(c.slot) * (ctx->polys[c.h].theta.size() - 1);
+    for (const Chain& c : ch) {
+      secs[c.l] += t_noise * double(c.slot) / npad_a;
+      if (!c.merged) continue;
+      const double w = double(c.slot) * (ctx->polys[c.h].theta.size() - 1);
+      secs[c.l] += work > 0 ? t_chain * w / work : 0.0;
+      mvs[c.l] += (long long)c.slot * (long long)(ctx->polys[c.h].theta.size() - 1);
+      for (int j = 0; j < n_noise[c.l]; ++j) x[c.l][j] += c.sign * v[c.r0 + j];
+    }
+  } else {
+    const double t_noise = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (const Chain& c : ch) secs[c.l] += t_noise * double(c.slot) / npad_a;
+  }
+  for (const Chain& c : ch) {
+    if (c.merged) continue;
+    const auto tc = std::chrono::steady_clock::now();
+    const long long mv0 = ctx->matvecs;
+    Run base;
+    base.g = geom_of(c.slot);
+    base.prec = prec;
+    base.codes = (const uint32_t*)codes + size_t(c.r0) * ga.V;
+    base.theta = theta_op;
+    base.partial = (double2*)part;
+    base.nbx = nbx;
+    CK(cudaMemsetAsync(part, 0, size_t(nbx) * c.slot * sizeof(double2), s));
+    const char* xc = (const char*)X + size_t(c.r0) * ga.V * 12 * elem;
+    TRY(apply_poly_impl(ctx, c.h, xc, n_noise[c.l], prec, ACC_BIL, nullptr, base, s));
+    std::vector<cd> v;
+    TRY(reduce_to_host(ctx, (double2*)part, nbx, 1, c.slot, v, s));
+    for (int j = 0; j < n_noise[c.l]; ++j) x[c.l][j] += c.sign * v[j];
+    secs[c.l] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tc).count();
+    mvs[c.l] += ctx->matvecs - mv0;
+  }
+  for (int l = 0; l < n_levels; ++l) {
+    // the level's noise: the slot of its first chain
+    int r0 = -1;
+    for (const Chain& c : ch)
+      if (c.l == l && r0 < 0) r0 = c.r0;
+    const geom gl = geom_of((n_noise[l] + R - 1) / R * R);
+    TRY(finish_level(ctx, hi[l], lo[l], theta_op, deflate, n_noise[l], gl, (const uint32_t*)codes + size_t(r0) * ga.V,
+                     prec, x[l], mvs[l], secs[l], &out[l], samples_out ? samples_out[l] : nullptr, s));
+  }
   return MMC_OK;
 }
 

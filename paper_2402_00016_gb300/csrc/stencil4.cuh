@@ -17,6 +17,13 @@
 //
 // Optionally (p.hint & 1) the result is stored with an L2 evict-first policy: it is
 // not read again by this launch, so L2 keeps the inputs instead.
+//
+// Link staging (SL, with 4 resident CTAs per SM): the eight links of each
+// site of an item are copied into shared memory (cp.async, 16-byte pieces, issued by the
+// site's own lanes at the start of the item, together with the first hop's spinor
+// loads) and every hop reads its link from there right before its products, so no
+// registers hold a link in flight and the prefetch of the next hop's spinor fits the
+// 128-register budget of 16 warps per SM.
 #pragma once
 #include <algorithm>
 
@@ -147,14 +154,38 @@ __device__ __forceinline__ void store_hint(S* p, const cx<typename StoreTraits<S
   }
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit_wait_all() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// A link from its five 16-byte pieces in shared memory (the FP32 link layout).
+__device__ __forceinline__ void load_link_shared(const float4* p, Link<float>& L) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = p[k];
+    L.u[2 * k] = cmake(v.x, v.y);
+    L.u[2 * k + 1] = cmake(v.z, v.w);
+  }
+  const float4 v = p[4];
+  L.u[8] = cmake(v.x, v.y);
+}
+
 // Hop D of the eight (0: x+, 1: x-, 2: y+, ..., 7: t-): project the spinor in `sp`,
 // start the loads of hop D+1 (or, after the last hop, of the own site) into `sp`
 // and `lk`, then multiply with the link of hop D and accumulate.
 // LATE: load the next link after the products (18 registers fewer, its latency not hidden).
-template <typename S, int R, int RPT, int KD, int D, bool LATE>
+// SL: the link of hop D comes from this site's staged links `sl` (8 x 5 pieces).
+template <typename S, int R, int RPT, int KD, int D, bool LATE, bool SL>
 __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in, int site, const int4& nf,
                                               const int4& nb, cx<typename StoreTraits<S>::R> (&sp)[12][RPT],
-                                              Link<typename StoreTraits<S>::R>& lk,
+                                              Link<typename StoreTraits<S>::R>& lk, const float4* sl,
                                               cx<typename StoreTraits<S>::R> (&acc)[12][RPT]) {
   using T = typename StoreTraits<S>::R;
   constexpr int MU = D / 2;
@@ -168,7 +199,13 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
   const int nsite = D == 7 ? site
                            : NBWD ? (NMU == 0 ? nb.x : NMU == 1 ? nb.y : NMU == 2 ? nb.z : nb.w)
                                   : (NMU == 0 ? nf.x : NMU == 1 ? nf.y : NMU == 2 ? nf.z : nf.w);
-  if constexpr (LATE) {
+  if constexpr (SL) {
+    Link<T> lc;
+    load_link_shared(sl + D * 5, lc);
+    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
+    multiply_add<T, RPT, MU, BWD, SG>(lc, h0, h1, acc);
+    fence_arr<T, RPT>(acc);
+  } else if constexpr (LATE) {
     load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
     multiply_add<T, RPT, MU, BWD, SG>(lk, h0, h1, acc);
     fence_arr<T, RPT>(acc);
@@ -184,11 +221,15 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
 
 // TH: the insertion Theta of the code bilinear when fixed at compile time (0: the
 // identity), -1 when read from p.theta.
-template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH>
+template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH, bool SL>
 __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_chunks, int n_items) {
   using T = float;
   constexpr int L = R / RPT;    // lanes per site
   constexpr int SPP = 128 / L;  // sites per item
+  // staged links: [site of the item][hop][piece]; a site's slot is written and read by
+  // its own L lanes only (one warp), so a warp-level barrier over them orders it
+  __shared__ __align__(16) float4 slink[SL ? SPP : 1][8][5];
+  const unsigned site_mask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << ((threadIdx.x & 31) / L * L);
   constexpr bool BIL = (ACC == ACC_CODES || ACC == ACC_LEFT);
   const int lane = threadIdx.x % L;
   const int r0 = lane * RPT;
@@ -282,16 +323,35 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
       for (int j = 0; j < RPT; ++j) acc[c][j] = cmake(T(0), T(0));
     cx<T> sp[12][RPT];
     Link<T> lk;
+    const float4* sl = &slink[SL ? threadIdx.x / L : 0][0][0];
+    if constexpr (SL) {
+      // the site's 8 links (forward at this site, backward at the neighbours) as 40
+      // pieces over its L lanes; the previous item's reads of the slot end first
+      __syncwarp(site_mask);
+      const float4* lsrc = reinterpret_cast<const float4*>(p.links);
+      for (int q = lane; q < 40; q += L) {
+        const int d = q / 5, k = q - 5 * (q / 5), mu = d >> 1;
+        const int nbs = mu == 0 ? nb.x : mu == 1 ? nb.y : mu == 2 ? nb.z : nb.w;
+        const int src = (d & 1) ? nbs : site;
+        cp_async16(smem_addr(sl + q), lsrc + (size_t(src) * 4 + mu) * 5 + k);
+      }
+    }
     load_spinor<S, R, RPT>(in + size_t(nf.x) * 12 * R, sp);
-    load_link(p.links, site, 0, lk);
-    hop_pipelined<S, R, RPT, KD, 0, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
-    hop_pipelined<S, R, RPT, KD, 1, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
-    hop_pipelined<S, R, RPT, KD, 2, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
-    hop_pipelined<S, R, RPT, KD, 3, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
-    hop_pipelined<S, R, RPT, KD, 4, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
-    hop_pipelined<S, R, RPT, KD, 5, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
-    hop_pipelined<S, R, RPT, KD, 6, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);
-    hop_pipelined<S, R, RPT, KD, 7, (MINB >= 4)>(p, in, site, nf, nb, sp, lk, acc);  // leaves the own spinor in sp
+    if constexpr (SL) {
+      cp_commit_wait_all();
+      __syncwarp(site_mask);
+    } else {
+      load_link(p.links, site, 0, lk);
+    }
+    constexpr bool LT = (MINB >= 4) && !SL;
+    hop_pipelined<S, R, RPT, KD, 0, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 1, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 2, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 3, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 4, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 5, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 6, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 7, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);  // leaves the own spinor in sp
 
     const size_t boff = rb_off + size_t(site) * 12 * R + r0;
     cx<T> si[RPT], so[RPT];
@@ -377,7 +437,7 @@ inline int resident_ctas(K kern) {
 
 // Dispatch of one (S, R) family over the epilogue modes (one rhs per lane); false
 // when the flags need another form.  nbx: rows of the bilinear partials (grid bound).
-template <typename S, int R, int MINB>
+template <typename S, int R, int MINB, bool SL>
 bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err) {
   constexpr int RPT = 1;
   const int f = p.flags;
@@ -390,23 +450,23 @@ bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_
   if ((f & SF_DAGGER) && (aux || acc != ACC_NONE)) return false;
   void (*kern)(step_params, int, int) = nullptr;
   if (f & SF_DAGGER) {
-    kern = step4_kernel<S, R, RPT, MINB, -1, false, ACC_NONE, -1>;
+    kern = step4_kernel<S, R, RPT, MINB, -1, false, ACC_NONE, -1, SL>;
   } else if (!aux) {
     switch (acc) {
-      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_NONE, -1>; break;
+      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_NONE, -1, SL>; break;
       case ACC_CODES:
-        kern = p.theta == 0 ? step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, 0>
-                            : step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, -1>;
+        kern = p.theta == 0 ? step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, 0, SL>
+                            : step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, -1, SL>;
         break;
-      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_Y, -1>; break;
-      default: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_LEFT, -1>; break;
+      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_Y, -1, SL>; break;
+      default: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_LEFT, -1, SL>; break;
     }
   } else {
     switch (acc) {
-      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_NONE, -1>; break;
-      case ACC_CODES: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_CODES, -1>; break;
-      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_Y, -1>; break;
-      default: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_LEFT, -1>; break;
+      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_NONE, -1, SL>; break;
+      case ACC_CODES: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_CODES, -1, SL>; break;
+      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_Y, -1, SL>; break;
+      default: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_LEFT, -1, SL>; break;
     }
   }
   constexpr int SPP = 128 / (R / RPT);

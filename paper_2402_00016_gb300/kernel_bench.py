@@ -38,6 +38,9 @@ def main(argv=None):
     ap.add_argument("--solve", type=int, default=0,
                     help="m > 0: time nrhs refined solves (FGMRES(8)) right-preconditioned by a degree m-1 "
                          "polynomial in Horner form (the step chains of the M^-1 level) instead of a level chain")
+    ap.add_argument("--solve-outer", type=int, default=2,
+                    help="FP64 refinement cycles of each timed solve (the launches are timed whether or not "
+                         "the solve converges in them)")
     ap.add_argument("--deflate", type=int, default=0,
                     help="k > 0: random deflation space of k vectors, levels deflated (tensor-core projections)")
     a = ap.parse_args(argv)
@@ -85,10 +88,16 @@ def main(argv=None):
                 if rep == 1:
                     mmc.mmc_profile(ctx, 1)
                 x.zero_()
-                its, rel = mmc.mmc_solve(ctx, b, x, a.nrhs, 1e-8, hp, prec, 8, 400)
+                try:
+                    its, rel = mmc.mmc_solve(ctx, b, x, a.nrhs, 1e-8, hp, prec, 8, a.solve_outer)
+                    converged = True
+                except mmc.MMCError as e:
+                    if e.code != mmc.MMC_ERR_NOCONV:
+                        raise
+                    its, converged = None, False
             p = mmc.mmc_profile_read(ctx)
             print(json.dumps({"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "solve_degree": a.solve - 1,
-                              "iterations": its, "step_launches": p["step_launches"],
+                              "iterations": its, "converged": converged, "step_launches": p["step_launches"],
                               "classes": mmc.mmc_profile_classes(ctx)}), flush=True)
             return
         variants = json.loads(a.sweep) if a.sweep else [None]

@@ -106,6 +106,8 @@ _SIGS = {
     "mmc_set_tensor_projections": (_i, [_vp, _i]),
     "mmc_trace_level": (_i, [_vp, _i, _i, _i, _i, _i, _u32, _u32, _i, _i,
                              ctypes.POINTER(mmc_level_stats), _dp]),
+    "mmc_trace_levels": (_i, [_vp, _i, _ip, _ip, _ip, ctypes.POINTER(_u32), ctypes.POINTER(_u32), _i, _i, _i,
+                              ctypes.POINTER(mmc_level_stats), ctypes.POINTER(_dp)]),
     "mmc_trace_exact": (_i, [_vp, _i, _i, _i, _i, _dp]),
     "mmc_estimate": (_i, [_vp, _i, ctypes.POINTER(mmc_level_spec), _i, _i, _i, _d, _i, _dp, _u32,
                           ctypes.POINTER(mmc_level_stats), _dp]),
@@ -333,6 +335,27 @@ def mmc_trace_level(ctx, hi, lo, theta_op, deflate, n_noise, first_noise, level,
     if want_samples:
         s["samples"] = samples[0::2] + 1j * samples[1::2]
     return s
+
+
+def mmc_trace_levels(ctx, his, los, theta_op, deflate, n_noises, first_noises, levels, prec, want_samples=True):
+    """Several polynomial levels in one batch; a list of per-level dicts as mmc_trace_level's."""
+    n = len(his)
+    if not (len(los) == len(n_noises) == len(first_noises) == len(levels) == n):
+        raise ValueError("per-level arguments must have the same length")
+    ia = lambda v: (ctypes.c_int * n)(*[int(x) for x in v])
+    ua = lambda v: (ctypes.c_uint32 * n)(*[int(x) for x in v])
+    st = (mmc_level_stats * n)()
+    bufs = [np.zeros(2 * int(k)) for k in n_noises] if want_samples else None
+    ptrs = (_dp * n)(*[b.ctypes.data_as(_dp) for b in bufs]) if want_samples else None
+    _check(lib.mmc_trace_levels(ctx, n, ia(his), ia(los), ia(n_noises), ua(first_noises), ua(levels),
+                                int(theta_op), int(deflate), int(prec), st, ptrs), ctx)
+    out = []
+    for l in range(n):
+        d = st[l].as_dict()
+        if want_samples:
+            d["samples"] = bufs[l][0::2] + 1j * bufs[l][1::2]
+        out.append(d)
+    return out
 
 
 def mmc_trace_exact(ctx, handle, theta_op, method, prec=MMC_F64):
