@@ -116,11 +116,13 @@ MATVECS_PER_SAMPLE = [28328 / 8, 14304 / 32, 20480 / 128, 20480 / 512]
 # DRAM traffic of the dominant step-kernel class, per site and right-hand side, from one ncu
 # capture per kernel form (dram__bytes_read.sum + dram__bytes_write.sum of a 64-rhs degree-8
 # level chain with the code bilinear at 24^4, the launch scaled to 512 rhs by site-rhs count):
-# keyed by (kernel version, traversal); a form without a capture reports null.
+# keyed by the kernel form; a form without a capture reports null.
 TRAFFIC_PER_SITE_RHS = {
-    # (kernel version, traversal, class kind, storage precision): bytes per site and rhs
-    (2, 1, "bilinear", 1): (4.671779e9 + 2.024867e9) / (331776 * 64),  # 315.4 B
-    (4, 2, "bilinear", 1): (3.195218e9 + 2.017202e9) / (331776 * 64),  # 245.5 B
+    # (kernel version, register cap, traversal, class kind, storage precision): bytes per site and rhs
+    (2, 4, 1, "bilinear", 1): (4.671779e9 + 2.024867e9) / (331776 * 64),  # 315.4 B
+    (4, 3, 2, "bilinear", 1): (3.220147e9 + 2.017138e9) / (331776 * 64),  # 246.6 B
+    # the Horner chains of the 8-rhs solves (one launch of the kernel_bench solve mode)
+    (4, 3, 0, "aux", 1): (669.179392e6 + 238.431744e6) / (331776 * 8),  # 341.9 B
 }
 
 
@@ -505,11 +507,14 @@ def main():
     dom = max(classes, key=lambda c: c["ms"]) if classes else None
     if dom and dom["ms"] > 0:
         achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
-        units = float(np.prod(W.dims)) * dom["nrhs_padded"]  # site-rhs per launch
+        # site-rhs per launch, averaged over the class's launches (a merged chain's launches
+        # shrink as its shorter polynomials finish): 1368 + 48 flops per site-rhs of a hop step
+        units = dom["flops"] / max(1, dom["launches"]) / (1368.0 + 48.0)
         rc = 1 if dom["nrhs_padded"] >= 16 else 0
         tkey = "%s_%s" % (("f64", "f32", "bf16")[dom["prec"]], "512rhs" if rc else "8rhs")
         form = tune.get(tkey, {}) if isinstance(tune, dict) else {}
-        tps = TRAFFIC_PER_SITE_RHS.get((form.get("version"), form.get("blocked"), dom["kind"], dom["prec"]))
+        tps = TRAFFIC_PER_SITE_RHS.get((form.get("version"), form.get("minb"), form.get("blocked"), dom["kind"],
+                                        dom["prec"]))
         traffic = tps * units if tps else None
     else:
         achieved, traffic, units, form = 0.0, None, 0, {}
@@ -529,8 +534,8 @@ def main():
                      "frac": achieved / peak,
                      "traffic": traffic,
                      "traffic_basis": ("DRAM bytes read and written per launch of this class's kernel form, "
-                                       "from one ncu capture of the same form on a 64-rhs case, scaled by "
-                                       "site-rhs to this launch" if traffic else
+                                       "from one ncu capture of the same form (a 64-rhs level chain, or an "
+                                       "8-rhs Horner chain), scaled by site-rhs to this launch" if traffic else
                                        "no DRAM counters were taken for this kernel form"),
                      "kernel": "step kernel (fused Wilson stencil + Leja step + epilogue), class %s, %s storage, "
                                "%d rhs per launch" % (dom["kind"], ("f64", "f32", "bf16")[dom["prec"]],

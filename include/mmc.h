@@ -240,9 +240,15 @@ int mmc_set_tensor_projections(mmc_ctx* ctx, int enable);
  * ||r|| <= rel_tol ||b|| per vector; inner right-preconditioned FGMRES(m_inner)
  * in precision prec_inner (MMC_F32 or MMC_BF16 storage with FP32 arithmetic;
  * MMC_F64 for the plain FP64 form) with
- * preconditioner p_h(M) (precond_handle, or MMC_ZERO for none).  x is the
- * initial guess on entry.  *iters receives inner iterations, relres_out (nrhs,
- * may be NULL) the final relative residuals. */
+ * preconditioner p_h(M) (precond_handle, or MMC_ZERO for none).  The FP64 form
+ * runs one FGMRES cycle per FP64 residual; with FP32/BF16 inner storage the
+ * inner solve restarts FGMRES(m_inner) from its own FP32 residual r - M e
+ * (deflated at every restart) for up to 8 cycles, until each vector's inner
+ * residual is 1e-3 of its FP64 residual (or what rel_tol still needs) or stops
+ * falling by 10% a cycle, so that one FP64 residual serves several cycles.
+ * max_outer bounds the FP64 residuals.  x is the initial guess on entry.
+ * *iters receives inner iterations (all cycles), relres_out (nrhs, may be
+ * NULL) the final relative residuals. */
 int mmc_solve(mmc_ctx* ctx, const void* b, void* x, int nrhs, double rel_tol, int precond_handle,
               int prec_inner, int m_inner, int max_outer, int* iters, double* relres_out);
 

@@ -358,6 +358,15 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     if (sr) CK(mmc::launch_salt_advance(ctx->salt, s));
     for (size_t k = 0; k < run.steps.size(); ++k) {
       const Step& st = run.steps[k];
+      // with per-block chain lengths the grid covers the blocks up to the last one still
+      // running (all of them when the longest chains come first); the others skip
+      int nrb_k = g.nrb;
+      if (!run.rb_len_host.empty()) {
+        nrb_k = 0;
+        for (int b = 0; b < int(run.rb_len_host.size()); ++b)
+          if (int(k) < run.rb_len_host[b]) nrb_k = b + 1;
+        if (nrb_k == 0) continue;
+      }
       mmc::step_params p;
       std::memset(&p, 0, sizeof(p));
       p.in = st.in;
@@ -401,8 +410,8 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
         cudaError_t e5 = cudaSuccess;
         const int ns = ctx->var_ns[run.prec][rc];
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
-        done = run.prec == MMC_F32 ? mmc::launch_step5_f32(g.R, ns == 3 ? 3 : 4, p, g.nrb, nbx, s, &e5)
-                                   : mmc::launch_step5_bf16(g.R, ns == 6 ? 6 : 4, p, g.nrb, nbx, s, &e5);
+        done = run.prec == MMC_F32 ? mmc::launch_step5_f32(g.R, ns == 3 ? 3 : 4, p, nrb_k, nbx, s, &e5)
+                                   : mmc::launch_step5_bf16(g.R, ns == 6 ? 6 : 4, p, nrb_k, nbx, s, &e5);
         CK(e5);
       }
       if (!done && ver_run == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
@@ -410,23 +419,23 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
         const int mbr = ctx->var_minb[run.prec][rc];
         const int mb = mbr == 3 ? 3 : (mbr == 5 ? 5 : 4);
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
-        done = run.prec == MMC_F32 ? mmc::launch_step4_f32(g.R, mb, p, g.nrb, nbx, s, &e4)
-                                   : mmc::launch_step4_bf16(g.R, mb, p, g.nrb, nbx, s, &e4);
+        done = run.prec == MMC_F32 ? mmc::launch_step4_f32(g.R, mb, p, nrb_k, nbx, s, &e4)
+                                   : mmc::launch_step4_bf16(g.R, mb, p, nrb_k, nbx, s, &e4);
         CK(e4);
       }
       if (!done && ver_run == 3 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e3 = cudaSuccess;
-        done = mmc::launch_step3(run.prec, g.R, rpt, run.nbx, ctx->var_ns[run.prec][rc], p, g.nrb, s, &e3);
+        done = mmc::launch_step3(run.prec, g.R, rpt, run.nbx, ctx->var_ns[run.prec][rc], p, nrb_k, s, &e3);
         CK(e3);
       }
       if (!done && ver_run >= 2 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e2 = cudaSuccess;
         const int mb = ctx->var_minb[run.prec][rc];
-        done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, mb, p, g.nrb, s, &e2)
-                                   : mmc::launch_step2_bf16(g.R, rpt, mb, p, g.nrb, s, &e2);
+        done = run.prec == MMC_F32 ? mmc::launch_step2_f32(g.R, rpt, mb, p, nrb_k, s, &e2)
+                                   : mmc::launch_step2_bf16(g.R, rpt, mb, p, nrb_k, s, &e2);
         CK(e2);
       }
-      if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec][rc], p, g.nrb, s));
+      if (!done) CK(mmc::launch_step(run.prec, rpt, ctx->var_minb[run.prec][rc], p, nrb_k, s));
       if (events) {
         CK(cudaEventRecord(e1, s));
         ctx->ev_pending.push_back({e0, e1, cls});
@@ -452,6 +461,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
     mix(reinterpret_cast<uintptr_t>(run.left));
     mix(reinterpret_cast<uintptr_t>(run.partial));
     mix(reinterpret_cast<uintptr_t>(run.rb_len));
+    for (int len : run.rb_len_host) mix(uint64_t(uint32_t(len)));
     mix(reinterpret_cast<uintptr_t>(run.prec == MMC_F64 ? ctx->links64 : ctx->links32));
     mix(uint64_t(run.theta) | (uint64_t(run.nbx) << 8) | (uint64_t(run.dagger) << 40) | (uint64_t(run.prec) << 48));
     mix(uint64_t(g.npad) | (uint64_t(g.R) << 32) | (uint64_t(ctx->stall_test) << 63));

@@ -1,6 +1,7 @@
 // Deflation (Sec. 7, Sec. 8), refined deflated solves (Sec. 1, Sec. 8), Monte
 // Carlo levels (Eq. 2, Sec. 6, Sec. 7), exact traces by unit vectors or
 // probing (Sec. 6) and the probing colouring search.
+#include <algorithm>
 #include <array>
 #include <chrono>
 #include <numeric>
@@ -69,19 +70,39 @@ int residual_f64(mmc_ctx* ctx, const geom& g, const void* b, const void* x, void
   return exec_run(ctx, run, s);
 }
 
+// ri = r32 - M e (FP32 storage): the same step launch as residual_f64 in FP32.
+int residual_f32(mmc_ctx* ctx, const geom& g, const void* r32, const void* e, void* ri, cudaStream_t s) {
+  Run run;
+  run.g = g;
+  run.prec = MMC_F32;
+  Step st;
+  st.in = e;
+  st.out = ri;
+  st.aux = r32;
+  st.flags = mmc::SF_HOP | mmc::SF_WRITE | mmc::SF_AUX;
+  st.coef = coef_block(g.npad);
+  for (int i = 0; i < g.npad; ++i) set_coef(st.coef, g.npad, i, -1.0, ctx->kappa, 1.0, 0, 0);
+  run.steps.push_back(st);
+  return exec_run(ctx, run, s);
+}
+
 // ------------------------------------------------------------------ solves
 // x += Z Lambda^-1 U^H r for every rhs (oblique eigen-projection of the residual).
 // fp32: projections and update from the FP32 copies of U and Z (inside a solve with
 // an FP32 inner stage; the next FP64 residual takes up their rounding); otherwise FP64.
-int deflate_residual(mmc_ctx* ctx, const geom& g, const void* r, void* x, bool fp32, cudaStream_t s) {
+// rx_prec: precision of the fields r and x (MMC_F64, or MMC_F32 inside the FP32 restarts of
+// a refined solve, which always take the FP32 copies).
+int deflate_residual(mmc_ctx* ctx, const geom& g, const void* r, void* x, bool fp32, cudaStream_t s,
+                     int rx_prec = MMC_F64) {
   const int k = ctx->k_defl;
   if (k == 0) return MMC_OK;
   fp32 = fp32 && ctx->U32 && ctx->Z32 && size_t(k) * g.R * 8 <= 48 * 1024;
+  if (rx_prec != MMC_F64 && !fp32) RET(MMC_ERR_ARG, "deflated FP32 residual needs the FP32 eigenvector copies");
   const int nbx = (g.V + kSpc - 1) / kSpc;
   void* part;
   TRY(scratch(ctx, "dr_part", size_t(nbx) * k * g.npad * sizeof(double2), &part));
   if (fp32)
-    CK(mmc::launch_vec_proj32(MMC_F64, g, (const float2*)ctx->U32, k, r, kSpc, (double2*)part, s));
+    CK(mmc::launch_vec_proj32(rx_prec, g, (const float2*)ctx->U32, k, r, kSpc, (double2*)part, s));
   else
     CK(mmc::launch_vec_proj(MMC_F64, g, ctx->U, k, r, kSpc, (double2*)part, s));
   std::vector<cd> c;
@@ -91,7 +112,7 @@ int deflate_residual(mmc_ctx* ctx, const geom& g, const void* r, void* x, bool f
   void* dc;
   TRY(upload(ctx, "dr_coef", c, &dc, s));
   if (fp32)
-    CK(mmc::launch_vec_update32(MMC_F64, g, (const float2*)ctx->Z32, k, (const double2*)dc, x, s));
+    CK(mmc::launch_vec_update32(rx_prec, g, (const float2*)ctx->Z32, k, (const double2*)dc, x, s));
   else
     CK(mmc::launch_vec_update(MMC_F64, g, ctx->Z, k, (const double2*)dc, x, s));
   return MMC_OK;
@@ -115,6 +136,74 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
   int inner = 0;
   rel.assign(nrhs, 0.0);
   const size_t stride = size_t(g.npad) * g.V * 12;  // elements per basis field
+  // One FGMRES(m) cycle on M e = v0 (v0 in the inner precision, already in Vb[0]): the
+  // correction e = sum_j y_j Z_j (Z = preconditioned basis) into ei.
+  auto op = [&](const void* vj, void* w) -> int {
+    const void* zj = vj;
+    if (precond != MMC_ZERO) {
+      const size_t j = (reinterpret_cast<const char*>(vj) - reinterpret_cast<const char*>(Vb)) / (stride * ebytes);
+      void* zdst = reinterpret_cast<char*>(Zb) + j * stride * ebytes;
+      Run base;
+      base.g = g;
+      if (is_net(ctx, precond)) {
+        if (ip != MMC_F32) RET(MMC_ERR_ARG, "mmc_solve: the learned preconditioner needs an FP32 inner solve");
+        TRY(net_apply(ctx, precond, vj, zdst, g.npad, s, nullptr));
+      } else if (ctx->polys[precond].kind == 0 && ctx->polys[precond].op == MMC_OP_M &&
+                 ctx->polys[precond].theta.size() >= 2) {
+        // single polynomial: Horner nesting, no accumulator field (3 field passes per degree)
+        const int hp = prec_inner == MMC_BF16 ? MMC_BF16 : ip;
+        void *Q0, *Q1, *src = const_cast<void*>(vj), *dst = zdst;
+        TRY(scratch(ctx, "sv_h0", field_bytes(g, hp), &Q0));
+        TRY(scratch(ctx, "sv_h1", field_bytes(g, hp), &Q1));
+        if (hp != ip) {
+          void* v16;
+          void* o16;
+          TRY(scratch(ctx, "sv_v16", field_bytes(g, hp), &v16));
+          TRY(scratch(ctx, "sv_o16", field_bytes(g, hp), &o16));
+          CK(mmc::launch_convert(hp, v16, ip, vj, g, s));
+          src = v16;
+          dst = o16;
+        }
+        base.prec = hp;
+        build_horner(ctx, base, ctx->polys[precond].theta, src, Q0, Q1, dst, g.npad);
+        TRY(exec_run(ctx, base, s));
+        if (hp != ip) CK(mmc::launch_convert(ip, zdst, hp, dst, g, s));
+      } else if (prec_inner == MMC_BF16) {
+        void* v16;
+        TRY(scratch(ctx, "sv_v16", field_bytes(g, MMC_BF16), &v16));
+        CK(mmc::launch_convert(MMC_BF16, v16, MMC_F32, vj, g, s));
+        base.prec = MMC_BF16;
+        TRY(apply_poly_impl(ctx, precond, v16, g.npad, MMC_BF16, ACC_Y, zdst, base, s));
+      } else {
+        base.prec = ip;
+        TRY(apply_poly_impl(ctx, precond, vj, g.npad, ip, ACC_Y, zdst, base, s));
+      }
+      zj = zdst;
+    }
+    return apply_M_impl(ctx, zj, w, g.npad, ip, false, s);
+  };
+  auto cycle = [&]() -> int {
+    ArnoldiOut ao;
+    TRY(arnoldi_cgs2(ctx, g, ip, Vb, m, op, ao, s));
+    inner += m;
+    std::vector<cd> ycoef(size_t(m) * g.npad, cd(0, 0));
+    for (int rr = 0; rr < g.npad; ++rr) {
+      if (ao.beta[rr] == 0) continue;
+      std::vector<cd> rhs(m + 1, cd(0, 0));
+      rhs[0] = ao.beta[rr];
+      double res;
+      std::vector<cd> y = mmc::hessenberg_lstsq(ao.H[rr], m, rhs, &res);
+      for (int j = 0; j < m; ++j) ycoef[size_t(j) * g.npad + rr] = -y[j];  // basis_update subtracts
+    }
+    void* dy;
+    TRY(upload(ctx, "sv_y", ycoef, &dy, s));
+    CK(cudaMemsetAsync(ei, 0, fi, s));
+    CK(mmc::launch_basis_update(ip, g, precond != MMC_ZERO ? Zb : Vb, stride, m, (const double2*)dy, ei, s));
+    return MMC_OK;
+  };
+  std::vector<cd> one(g.npad, cd(1, 0));
+  void* d1;
+  TRY(upload(ctx, "sv_one", one, &d1, s));
   for (int outer = 0; outer <= max_outer; ++outer) {
     TRY(residual_f64(ctx, g, b, x, r, s));
     if (ctx->k_defl > 0) {
@@ -133,73 +222,52 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
       return MMC_OK;
     }
     if (outer == max_outer) break;
-    // inner right-preconditioned FGMRES(m) cycle on M e = r
-    CK(mmc::launch_convert(ip, Vb, MMC_F64, r, g, s));
-    auto op = [&](const void* vj, void* w) -> int {
-      const void* zj = vj;
-      if (precond != MMC_ZERO) {
-        const size_t j = (reinterpret_cast<const char*>(vj) - reinterpret_cast<const char*>(Vb)) / (stride * ebytes);
-        void* zdst = reinterpret_cast<char*>(Zb) + j * stride * ebytes;
-        Run base;
-        base.g = g;
-        if (is_net(ctx, precond)) {
-          if (ip != MMC_F32) RET(MMC_ERR_ARG, "mmc_solve: the learned preconditioner needs an FP32 inner solve");
-          TRY(net_apply(ctx, precond, vj, zdst, g.npad, s, nullptr));
-        } else if (ctx->polys[precond].kind == 0 && ctx->polys[precond].op == MMC_OP_M &&
-                   ctx->polys[precond].theta.size() >= 2) {
-          // single polynomial: Horner nesting, no accumulator field (3 field passes per degree)
-          const int hp = prec_inner == MMC_BF16 ? MMC_BF16 : ip;
-          void *Q0, *Q1, *src = const_cast<void*>(vj), *dst = zdst;
-          TRY(scratch(ctx, "sv_h0", field_bytes(g, hp), &Q0));
-          TRY(scratch(ctx, "sv_h1", field_bytes(g, hp), &Q1));
-          if (hp != ip) {
-            void* v16;
-            void* o16;
-            TRY(scratch(ctx, "sv_v16", field_bytes(g, hp), &v16));
-            TRY(scratch(ctx, "sv_o16", field_bytes(g, hp), &o16));
-            CK(mmc::launch_convert(hp, v16, ip, vj, g, s));
-            src = v16;
-            dst = o16;
-          }
-          base.prec = hp;
-          build_horner(ctx, base, ctx->polys[precond].theta, src, Q0, Q1, dst, g.npad);
-          TRY(exec_run(ctx, base, s));
-          if (hp != ip) CK(mmc::launch_convert(ip, zdst, hp, dst, g, s));
-        } else if (prec_inner == MMC_BF16) {
-          void* v16;
-          TRY(scratch(ctx, "sv_v16", field_bytes(g, MMC_BF16), &v16));
-          CK(mmc::launch_convert(MMC_BF16, v16, MMC_F32, vj, g, s));
-          base.prec = MMC_BF16;
-          TRY(apply_poly_impl(ctx, precond, v16, g.npad, MMC_BF16, ACC_Y, zdst, base, s));
-        } else {
-          base.prec = ip;
-          TRY(apply_poly_impl(ctx, precond, vj, g.npad, ip, ACC_Y, zdst, base, s));
-        }
-        zj = zdst;
-      }
-      return apply_M_impl(ctx, zj, w, g.npad, ip, false, s);
-    };
-    ArnoldiOut ao;
-    TRY(arnoldi_cgs2(ctx, g, ip, Vb, m, op, ao, s));
-    inner += m;
-    std::vector<cd> ycoef(size_t(m) * g.npad, cd(0, 0));
-    for (int rr = 0; rr < g.npad; ++rr) {
-      if (ao.beta[rr] == 0) continue;
-      std::vector<cd> rhs(m + 1, cd(0, 0));
-      rhs[0] = ao.beta[rr];
-      double res;
-      std::vector<cd> y = mmc::hessenberg_lstsq(ao.H[rr], m, rhs, &res);
-      for (int j = 0; j < m; ++j) ycoef[size_t(j) * g.npad + rr] = -y[j];  // basis_update subtracts
+    if (ip == MMC_F64) {
+      // the plain FP64 form: one FGMRES(m) cycle per FP64 residual
+      CK(mmc::launch_convert(ip, Vb, MMC_F64, r, g, s));
+      TRY(cycle());
+      CK(mmc::launch_axpby(MMC_F64, g, (const double2*)d1, ei, (const double2*)d1, x, s));
+      continue;
     }
-    void* dy;
-    TRY(upload(ctx, "sv_y", ycoef, &dy, s));
-    CK(cudaMemsetAsync(ei, 0, fi, s));
-    CK(mmc::launch_basis_update(ip, g, precond != MMC_ZERO ? Zb : Vb, stride, m, (const double2*)dy, ei, s));
-    if (ip != MMC_F64) CK(mmc::launch_convert(MMC_F64, e64, ip, ei, g, s));
-    std::vector<cd> one(g.npad, cd(1, 0));
-    void* d1;
-    TRY(upload(ctx, "sv_one", one, &d1, s));
-    CK(mmc::launch_axpby(MMC_F64, g, (const double2*)d1, ip == MMC_F64 ? ei : e64, (const double2*)d1, x, s));
+    // Mixed precision: restarted FGMRES(m) cycles on M e = r in FP32, each later one restarted
+    // from the FP32 residual r - M e (with deflation, from its deflated form), until every
+    // vector's residual is kInnerReduction of the FP64 one (or what the tolerance still
+    // needs), stagnates, or kInnerCycles cycles ran; then x += e and one FP64 residual.
+    // FP64 M applications (the FP64 pipe is 1/62 of the FP32 one) fall from one or two per
+    // cycle to one or two per refinement step.
+    const double kInnerReduction = 1e-3;
+    const int kInnerCycles = 8;
+    void *r32, *ri, *et;
+    TRY(scratch(ctx, "sv_r32", fi, &r32));
+    TRY(scratch(ctx, "sv_ri32", fi, &ri));
+    TRY(scratch(ctx, "sv_et32", fi, &et));
+    CK(mmc::launch_convert(MMC_F32, r32, MMC_F64, r, g, s));
+    CK(cudaMemcpyAsync(ri, r32, fi, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(et, 0, fi, s));
+    std::vector<double> tgt(nrhs), prev(rn2.begin(), rn2.begin() + nrhs), ri2;
+    for (int i = 0; i < nrhs; ++i)
+      tgt[i] = std::max(kInnerReduction * kInnerReduction * rn2[i], 0.25 * tol * tol * bn2[i]);
+    for (int cyc = 0; cyc < kInnerCycles; ++cyc) {
+      if (ctx->k_defl > 0 && cyc > 0) {  // the first cycle starts from the deflated FP64 residual
+        TRY(deflate_residual(ctx, g, ri, et, true, s, MMC_F32));
+        TRY(residual_f32(ctx, g, r32, et, ri, s));
+      }
+      CK(cudaMemcpyAsync(Vb, ri, fi, cudaMemcpyDeviceToDevice, s));
+      TRY(cycle());
+      CK(mmc::launch_axpby(MMC_F32, g, (const double2*)d1, ei, (const double2*)d1, et, s));
+      TRY(residual_f32(ctx, g, r32, et, ri, s));
+      TRY(norms2(ctx, MMC_F32, g, ri, ri2, s));
+      bool ok = true, moving = false;
+      for (int i = 0; i < nrhs; ++i) {
+        if (!std::isfinite(ri2[i])) RET(MMC_ERR_NAN, "mmc_solve: NaN in the inner residual");
+        if (ri2[i] > tgt[i]) ok = false;
+        if (ri2[i] > tgt[i] && ri2[i] < 0.81 * prev[i]) moving = true;  // norm still falls by 10% a cycle
+        prev[i] = ri2[i];
+      }
+      if (ok || !moving) break;
+    }
+    CK(mmc::launch_convert(MMC_F64, e64, MMC_F32, et, g, s));
+    CK(mmc::launch_axpby(MMC_F64, g, (const double2*)d1, e64, (const double2*)d1, x, s));
   }
   if (iters) *iters = inner;
   RET(MMC_ERR_NOCONV, "mmc_solve: relative residual above tolerance after max_outer cycles");
@@ -859,6 +927,13 @@ int mmc_trace_levels(mmc_ctx* ctx, int n_levels, const int* hi, const int* lo, c
         ch.push_back({l, h, side == 0 ? 1.0 : -1.0, merged, 0, 0});
         nsum += n_noise[l];
       }
+  // the longest merged chains first: the blocks still running at any step are a prefix,
+  // so every launch's grid covers exactly them
+  std::stable_sort(ch.begin(), ch.end(), [&](const Chain& a, const Chain& b) {
+    if (a.merged != b.merged) return a.merged;
+    if (!a.merged) return false;
+    return ctx->polys[a.h].theta.size() > ctx->polys[b.h].theta.size();
+  });
   if (nsum > (1ll << 24)) RET(MMC_ERR_ARG, "mmc_trace_levels: too many noise vectors in one batch");
   const int R = rhs_block(int(nsum), ctx->rhs_max);
   int npad_m = 0, npad_a = 0;

@@ -95,6 +95,25 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
     cx<T> si[RPT], so[RPT];
 #pragma unroll
     for (int j = 0; j < RPT; ++j) si[j] = so[j] = cmake(T(0), T(0));
+    // the aux operand's and the accumulator's 12 components, all loaded before the first
+    // store of the pass (the compiler keeps loads that may alias the stores behind them,
+    // one memory latency per component)
+    cx<T> axv[AUX ? 12 : 1][RPT];
+    if (AUX) {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) load_rpt<S, RPT>(reinterpret_cast<const S*>(p.aux) + boff + c * R, axv[c]);
+    }
+    cx<T> yv[ACC == ACC_Y ? 12 : 1][RPT];
+    if (ACC == ACC_Y) {
+      const float2* yp = reinterpret_cast<const float2*>(p.y) + boff;
+#pragma unroll
+      for (int c = 0; c < 12; ++c)
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+          const float2 t = yp[c * R + j];
+          yv[c][j] = cmake(t.x, t.y);
+        }
+    }
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       cx<T> vin[RPT], vout[RPT];
@@ -102,10 +121,8 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
 #pragma unroll
       for (int j = 0; j < RPT; ++j) vout[j] = cfma(cb[j], acc[c][j], cmul(ca[j], vin[j]));
       if (AUX) {
-        cx<T> ax[RPT];
-        load_rpt<S, RPT>(reinterpret_cast<const S*>(p.aux) + boff + c * R, ax);
 #pragma unroll
-        for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], ax[j], vout[j]);
+        for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], axv[AUX ? c : 0][j], vout[j]);
       }
       if (std::is_same<S, __nv_bfloat162>::value && p.salt)
         store_rpt_sr<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout, srkey, uint32_t(boff + c * R));
@@ -115,8 +132,7 @@ __global__ void __launch_bounds__(128, MINB) step2_kernel(step_params p) {
         float2* yp = reinterpret_cast<float2*>(p.y) + boff + c * R;
 #pragma unroll
         for (int j = 0; j < RPT; ++j) {
-          float2 yv = yp[j];
-          cx<T> a = cmake(yv.x, yv.y);
+          cx<T> a = yv[ACC == ACC_Y ? c : 0][j];
           a = cfma(cwi[j], vin[j], a);
           if (bil_out) a = cfma(cwo[j], vout[j], a);
           yp[j] = make_float2(a.re, a.im);

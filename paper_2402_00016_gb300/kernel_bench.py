@@ -38,6 +38,9 @@ def main(argv=None):
     ap.add_argument("--solve", type=int, default=0,
                     help="m > 0: time nrhs refined solves (FGMRES(8)) right-preconditioned by a degree m-1 "
                          "polynomial in Horner form (the step chains of the M^-1 level) instead of a level chain")
+    ap.add_argument("--apply", action="store_true",
+                    help="time p(M) X as a vector (the accumulating chain, mmc_apply_poly) instead of a level "
+                         "chain's bilinear")
     ap.add_argument("--solve-outer", type=int, default=2,
                     help="FP64 refinement cycles of each timed solve (the launches are timed whether or not "
                          "the solve converges in them)")
@@ -109,16 +112,27 @@ def main(argv=None):
                 for rc in (0, 1):
                     mmc.mmc_set_step_variant_class(ctx, prec, rc, v)
                 mmc.mmc_set_step_variant(ctx, prec, 0, 400 + int(var.get("hint", 0)), 0)
-            mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, 0, 1, prec)  # warm-up
+            if a.apply:
+                xa = mmc.new_field(ctx, a.nrhs, prec)
+                ya = mmc.new_field(ctx, a.nrhs, prec)
+                mmc.mmc_noise(ctx, 1, 0, mmc.MMC_TAG_NOISE, a.nrhs, prec, xa)
+
+            def one(r):
+                if a.apply:
+                    mmc.mmc_apply_poly(ctx, h, xa, ya, a.nrhs, prec)
+                else:
+                    mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, a.nrhs * r, 1, prec)
+
+            one(0)  # warm-up
             mmc.mmc_profile(ctx, 1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for r in range(a.reps):
-                mmc.mmc_trace_level(ctx, h, h2, 0, defl, a.nrhs, a.nrhs * (r + 1), 1, prec)
+                one(r + 1)
             e1.record()
             torch.cuda.synchronize()
             p = mmc.mmc_profile_read(ctx)
-            out = {"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "degree": a.degree,
+            out = {"dims": a.dims, "nrhs": a.nrhs, "prec": a.prec, "degree": a.degree, "apply": a.apply,
                    "graphs": a.graphs, "rmax": a.rmax,
                    "step_launches": p["step_launches"], "avg_launch_ms": p["step_ms"] / max(1, p["step_launches"]),
                    "algorithmic_GBps": p["step_bytes"] / p["step_ms"] / 1e6 if p["step_ms"] else 0,
