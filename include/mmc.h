@@ -244,8 +244,9 @@ int mmc_set_tensor_projections(mmc_ctx* ctx, int enable);
  * runs one FGMRES cycle per FP64 residual; with FP32/BF16 inner storage the
  * inner solve restarts FGMRES(m_inner) from its own FP32 residual r - M e
  * (deflated at every restart) for up to 8 cycles, until each vector's inner
- * residual is 1e-3 of its FP64 residual (or what rel_tol still needs) or stops
- * falling by 10% a cycle, so that one FP64 residual serves several cycles.
+ * residual is 3e-2 of its FP64 residual (or what rel_tol still needs) or stops
+ * falling by 10% a cycle, so that one FP64 residual serves several cycles
+ * (mmc_set_solve_refinement).
  * max_outer bounds the FP64 residuals.  x is the initial guess on entry.
  * *iters receives inner iterations (all cycles), relres_out (nrhs, may be
  * NULL) the final relative residuals. */
@@ -425,6 +426,13 @@ int mmc_profile_classes(mmc_ctx* ctx, int max_classes, mmc_profile_class* out, i
  * (Sec. 1 and Sec. 8: the solves of the M^-1 level; defaults 48 and 400).
  * Values <= 0 keep the current setting. */
 int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
+/* Schedule of the FP32/BF16 stage of the refined solves (mmc_solve and the solves of
+ * mmc_trace_level): after each FP64 residual, up to inner_cycles FGMRES cycles, each
+ * later one restarted from the stage's own FP32 residual (deflated), until every
+ * vector's inner residual is inner_reduction (in (0, 1]) of its FP64 residual or stops
+ * falling by 10% a cycle.  inner_cycles = 1 returns to FP64 after every cycle.
+ * Defaults 3e-2 and 8.  MMC_ERR_ARG outside 1..64 cycles or (0, 1]. */
+int mmc_set_solve_refinement(mmc_ctx* ctx, double inner_reduction, int inner_cycles);
 /* Storage of the inner FGMRES stage (its preconditioner chain included) in the
  * solves of the M^-1 level of a reduced-precision mmc_trace_level (Sec. 1,
  * Sec. 8; the prec_inner of mmc_solve): MMC_F32 (default) or MMC_BF16.  The FP64

@@ -266,6 +266,15 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer) {
   return MMC_OK;
 }
 
+int mmc_set_solve_refinement(mmc_ctx* ctx, double inner_reduction, int inner_cycles) {
+  if (!ctx) return MMC_ERR_ARG;
+  if (!(inner_reduction > 0.0 && inner_reduction <= 1.0) || inner_cycles < 1 || inner_cycles > 64)
+    RET(MMC_ERR_ARG, "mmc_set_solve_refinement: reduction in (0, 1], cycles 1..64");
+  ctx->solve_red = inner_reduction;
+  ctx->solve_cycles = inner_cycles;
+  return MMC_OK;
+}
+
 int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters) {
   if (!ctx || wait_iters < 0) return MMC_ERR_ARG;
   ctx->stall_test = enable != 0;
@@ -489,13 +498,14 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
       }
     }
     // the persistent, pipelined form (version 4, one rhs per lane): register caps (3: 168
-    // registers, 4: 128, 5: 128 with the links staged in shared memory) and traversals
+    // registers; 4: 128; 5: 128 with the links staged in shared memory) and traversals
     for (int ordr = 0; ordr <= 2; ++ordr)
     for (int mb = 3; mb <= 5; ++mb) {
       if ((ordr == 1 && !ctx->order) || (ordr == 2 && !ctx->order_zh)) continue;
       ctx->var_ver[prec][rc] = 4;
       ctx->var_rpt[prec][rc] = 1;
       ctx->var_minb[prec][rc] = mb;
+      ctx->var_ns[prec][rc] = 0;
       ctx->order_v[prec][rc] = ordr;
       TRY(time_variant());
       if (med < best_ms) {
@@ -503,6 +513,7 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
         bv = 4;
         br = 1;
         bm = mb;
+        bn = 0;
         bo = ordr;
       }
     }

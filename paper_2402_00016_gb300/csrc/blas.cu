@@ -329,6 +329,69 @@ __global__ void basis_update_kernel(geom g, const T* A, size_t a_stride, int nve
   for (int c = 0; c < 12; ++c) put<T>(w, fidx(g, rb, site, c, r), acc[c].x, acc[c].y);
 }
 
+// The basis update of a Gram-Schmidt pass fused with the dot products that follow it:
+// w <- w - sum_i h_i A_i (nvec <= 8 basis fields), then, from the updated w still in
+// registers, either partial[b][i] = sum A_i^H w (the next pass's projections, NORM
+// false) or partial[b][0] = w^H w (NORM true), per CTA of spc sites as multidot_kernel
+// lays them out.  One read of A and w instead of two.
+template <bool NORM>
+__global__ void update_dot_kernel(geom g, const float2* A, size_t a_stride, int nvec, const double2* h, float2* w,
+                                  int spc, double2* partial) {
+  constexpr int NB = 8;
+  __shared__ double2 sh[8 * 32];
+  const int rb = blockIdx.y;
+  const int r = threadIdx.x % g.R;
+  const int spp = blockDim.x / g.R;
+  const int rg = rb * g.R + r;
+  float hx[NB], hy[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const double2 hd = q < nvec ? h[size_t(q) * g.npad + rg] : make_double2(0.0, 0.0);
+    hx[q] = float(hd.x);
+    hy[q] = float(hd.y);
+  }
+  float re[NB], im[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) re[q] = im[q] = 0.f;
+  const int s_begin = blockIdx.x * spc, s_end = min(g.V, s_begin + spc);
+  for (int s0 = s_begin; s0 < s_end; s0 += spp) {
+    const int site = s0 + threadIdx.x / g.R;
+    if (site >= s_end) continue;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const size_t e = fidx(g, rb, site, c, r);
+      float2 x = w[e];
+      float2 a[NB];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < nvec) {
+          a[q] = A[size_t(q) * a_stride + e];
+          x.x -= a[q].x * hx[q] - a[q].y * hy[q];
+          x.y -= a[q].x * hy[q] + a[q].y * hx[q];
+        }
+      }
+      w[e] = x;
+      if (NORM) {
+        re[0] += x.x * x.x + x.y * x.y;
+      } else {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          if (q < nvec) {
+            re[q] += a[q].x * x.x + a[q].y * x.y;
+            im[q] += a[q].x * x.y - a[q].y * x.x;
+          }
+        }
+      }
+    }
+  }
+  const int nout = NORM ? 1 : nvec;
+  for (int q = 0; q < nout; ++q) {
+    double dre = re[q], dim = im[q];
+    cta_reduce_r(dre, dim, g.R, sh);
+    if (threadIdx.x < g.R) partial[(size_t(blockIdx.x) * nout + q) * g.npad + rb * g.R + threadIdx.x] = make_double2(dre, dim);
+  }
+}
+
 template <typename T>
 __global__ void normalise_kernel(geom g, const T* src, const double2* nrm2, T* dst) {
   const int rb = blockIdx.y;
@@ -758,6 +821,18 @@ cudaError_t launch_normalise(int prec, geom g, const void* src, const double2* n
     normalise_kernel<double2><<<grid, 256, 0, s>>>(g, (const double2*)src, nrm2, (double2*)dst);
   else
     normalise_kernel<float2><<<grid, 256, 0, s>>>(g, (const float2*)src, nrm2, (float2*)dst);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_dot(geom g, const float2* A, size_t a_stride, int nvec, const double2* h, float2* w,
+                              bool norm, int spc, double2* partial, cudaStream_t s) {
+  if (nvec < 1 || nvec > 8) return cudaErrorInvalidValue;
+  dim3 grid((g.V + spc - 1) / spc, g.nrb);
+  if (norm)
+    update_dot_kernel<true><<<grid, 256, 0, s>>>(g, A, a_stride, nvec, h, w, spc, partial);
+  else
+    update_dot_kernel<false><<<grid, 256, 0, s>>>(g, A, a_stride, nvec, h, w, spc, partial);
   count_launch();
   return cudaGetLastError();
 }

@@ -96,6 +96,8 @@ struct mmc_ctx {
   double defl_max_u = 100.0;  // mmc_deflate: bound on the norm of a left vector u_i (a column of (W^H Z)^{-H})
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
+  double solve_red = 3e-2;   // FP32 stage of the refined solves: gain per FP64 residual
+  int solve_cycles = 8;      // and its most FGMRES cycles
   long long wait_iters = 0;   // bound of the staged kernel's mbarrier waits (0: its default)
   int stall_test = 0;         // fault injection for tests: the staged kernel's producer copies nothing
   int rhs_max = 16;           // largest rhs block R of the blocked field layout (8 or 16)
@@ -845,12 +847,23 @@ inline int arnoldi_cgs2(mmc_ctx* ctx, const geom& g, int prec, void* V, int m, O
     double2* hc = reinterpret_cast<double2*>(hcols) + size_t(j) * (m + 1) * g.npad;
     CK(mmc::launch_multidot(prec, g, V, stride, j + 1, W, 0, spc, (double2*)part, s));
     CK(mmc::launch_reduce((double2*)part, nbx, j + 1, g.npad, (double2*)h1, 0, s));
-    CK(mmc::launch_basis_update(prec, g, V, stride, j + 1, (double2*)h1, W, s));
-    CK(mmc::launch_multidot(prec, g, V, stride, j + 1, W, 0, spc, (double2*)part, s));
-    CK(mmc::launch_reduce((double2*)part, nbx, j + 1, g.npad, (double2*)h2, 0, s));
-    CK(mmc::launch_basis_update(prec, g, V, stride, j + 1, (double2*)h2, W, s));
-    CK(mmc::launch_add2((double2*)h1, (double2*)h2, hc, (j + 1) * g.npad, s));
-    CK(mmc::launch_multidot(prec, g, W, stride, 1, W, 0, spc, (double2*)part, s));
+    if (prec == MMC_F32 && j + 1 <= 8) {
+      // FP32 basis: each update fused with the dot products that follow it (the second
+      // pass's projections, then the norm), one read of the basis and of w each
+      CK(mmc::launch_update_dot(g, (const float2*)V, stride, j + 1, (double2*)h1, (float2*)W, false, spc,
+                                (double2*)part, s));
+      CK(mmc::launch_reduce((double2*)part, nbx, j + 1, g.npad, (double2*)h2, 0, s));
+      CK(mmc::launch_update_dot(g, (const float2*)V, stride, j + 1, (double2*)h2, (float2*)W, true, spc,
+                                (double2*)part, s));
+      CK(mmc::launch_add2((double2*)h1, (double2*)h2, hc, (j + 1) * g.npad, s));
+    } else {
+      CK(mmc::launch_basis_update(prec, g, V, stride, j + 1, (double2*)h1, W, s));
+      CK(mmc::launch_multidot(prec, g, V, stride, j + 1, W, 0, spc, (double2*)part, s));
+      CK(mmc::launch_reduce((double2*)part, nbx, j + 1, g.npad, (double2*)h2, 0, s));
+      CK(mmc::launch_basis_update(prec, g, V, stride, j + 1, (double2*)h2, W, s));
+      CK(mmc::launch_add2((double2*)h1, (double2*)h2, hc, (j + 1) * g.npad, s));
+      CK(mmc::launch_multidot(prec, g, W, stride, 1, W, 0, spc, (double2*)part, s));
+    }
     CK(mmc::launch_reduce((double2*)part, nbx, 1, g.npad, nrm2 + size_t(j + 1) * g.npad, 0, s));
     CK(mmc::launch_normalise(prec, g, W, nrm2 + size_t(j + 1) * g.npad, Vb + size_t(j + 1) * stride * eb, s));
   }

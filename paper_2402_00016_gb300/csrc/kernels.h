@@ -79,6 +79,10 @@ cudaError_t launch_reduce(const double2* partial, int nbx, int nvec, int npad, d
 // w -= sum_i A_i * h[i][r] (h device, double2 [nvec][npad]).
 cudaError_t launch_basis_update(int prec, geom g, const void* A, size_t a_stride, int nvec, const double2* h,
                                 void* w, cudaStream_t s);
+// FP32 fields: w <- w - sum_i h_i A_i (nvec <= 8), then per-CTA partials (rows of spc
+// sites, as launch_multidot) of A_i^H w (norm false, nvec rows) or of w^H w (norm true).
+cudaError_t launch_update_dot(geom g, const float2* A, size_t a_stride, int nvec, const double2* h, float2* w,
+                              bool norm, int spc, double2* partial, cudaStream_t s);
 // dst = scale(r) * src with scale = 1 / sqrt(nrm2[r].x), zero if nrm2 == 0.
 cudaError_t launch_normalise(int prec, geom g, const void* src, const double2* nrm2, void* dst, cudaStream_t s);
 // y = a[r] * x + b[r] * y (complex per-rhs coefficients on the device).

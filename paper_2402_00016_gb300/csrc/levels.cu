@@ -231,12 +231,12 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
     }
     // Mixed precision: restarted FGMRES(m) cycles on M e = r in FP32, each later one restarted
     // from the FP32 residual r - M e (with deflation, from its deflated form), until every
-    // vector's residual is kInnerReduction of the FP64 one (or what the tolerance still
-    // needs), stagnates, or kInnerCycles cycles ran; then x += e and one FP64 residual.
+    // vector's residual is solve_red of the FP64 one (or what the tolerance still needs),
+    // stagnates, or solve_cycles cycles ran; then x += e and one FP64 residual.
     // FP64 M applications (the FP64 pipe is 1/62 of the FP32 one) fall from one or two per
     // cycle to one or two per refinement step.
-    const double kInnerReduction = 1e-3;
-    const int kInnerCycles = 8;
+    const double kInnerReduction = ctx->solve_red;
+    const int kInnerCycles = ctx->solve_cycles;
     void *r32, *ri, *et;
     TRY(scratch(ctx, "sv_r32", fi, &r32));
     TRY(scratch(ctx, "sv_ri32", fi, &ri));

@@ -130,6 +130,7 @@ _SIGS = {
     "mmc_test_stall_staged": (_i, [_vp, _i, ctypes.c_longlong]),
     "mmc_graph_note": (ctypes.c_char_p, [_vp]),
     "mmc_set_solve_params": (_i, [_vp, _i, _i]),
+    "mmc_set_solve_refinement": (_i, [_vp, _d, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
     "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
     "mmc_leja_order": (_i, [_i, _dp, _dp]),
@@ -458,6 +459,10 @@ def mmc_set_solve_storage(ctx, prec_inner):
 
 def mmc_set_solve_params(ctx, m_inner=0, max_outer=0):
     _check(lib.mmc_set_solve_params(ctx, int(m_inner), int(max_outer)), ctx)
+
+
+def mmc_set_solve_refinement(ctx, inner_reduction, inner_cycles):
+    _check(lib.mmc_set_solve_refinement(ctx, float(inner_reduction), int(inner_cycles)), ctx)
 
 
 def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):

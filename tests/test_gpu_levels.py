@@ -108,22 +108,32 @@ def test_level_double_poly_vs_zero(mmc, lat):
     assert (np.abs(st["samples"] - want) / scale).max() < 1e-11
 
 
-def test_solve_refined(mmc, lat):
-    """Inner FP32 FGMRES with FP64 defect correction reaches 1e-10 (residual checked by the oracle's M)."""
+@pytest.mark.parametrize("sched", [(1.0, 1), (3e-2, 8), (1e-3, 8)])
+def test_solve_refined(mmc, lat, sched):
+    """Inner FP32 FGMRES with FP64 defect correction reaches 1e-10 (residual checked by the
+    oracle's M) with every schedule of the FP32 stage: one cycle per FP64 residual, and
+    restarts from the FP32 residual until it has gained 3e-2 or 1e-3."""
     nrhs = 3
     b = mmc.new_field(lat.ctx, nrhs, 0)
     x = mmc.new_field(lat.ctx, nrhs, 0)
     mmc.mmc_noise(lat.ctx, 1, 0, mmc.MMC_TAG_NOISE, nrhs, 0, b)
     hp, _ = mmc.mmc_gmres_poly(lat.ctx, 6)
-    for pre in (mmc.MMC_ZERO, hp):
-        x.zero_()
-        its, rel = mmc.mmc_solve(lat.ctx, b, x, nrhs, 1e-10, pre, mmc.MMC_F32, 24, 100)
-        xs = mmc.mmc_unpack(lat.ctx, x, nrhs, 0, lat.V)
-        for j in range(nrhs):
-            e = lat.eta(j, 1)
-            r = np.linalg.norm(e - lat.op(xs[j])) / np.linalg.norm(e)
-            assert r <= 1.05e-10, r
-            assert rel[j] <= 1e-10
+    mmc.mmc_set_solve_refinement(lat.ctx, *sched)
+    try:
+        for pre in (mmc.MMC_ZERO, hp):
+            x.zero_()
+            its, rel = mmc.mmc_solve(lat.ctx, b, x, nrhs, 1e-10, pre, mmc.MMC_F32, 24, 100)
+            xs = mmc.mmc_unpack(lat.ctx, x, nrhs, 0, lat.V)
+            for j in range(nrhs):
+                e = lat.eta(j, 1)
+                r = np.linalg.norm(e - lat.op(xs[j])) / np.linalg.norm(e)
+                assert r <= 1.05e-10, r
+                assert rel[j] <= 1e-10
+        for bad in ((0.0, 8), (1.5, 8), (0.1, 0), (0.1, 65)):
+            with pytest.raises(mmc.MMCError):
+                mmc.mmc_set_solve_refinement(lat.ctx, *bad)
+    finally:
+        mmc.mmc_set_solve_refinement(lat.ctx, 3e-2, 8)
 
 
 @pytest.mark.parametrize("prec,inner", [(0, 1), (1, 1), (1, 2)])
