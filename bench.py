@@ -352,6 +352,7 @@ def main():
             hn16, hist = learned_train.train(mmc, c16, eta16, xs16, args.learned_pairs, iters=args.learned_iters)
             weights = mmc.mmc_net_get_weights(c16, hn16)
             del eta16, xs16
+            torch.cuda.empty_cache()  # the 4096 training pairs (51 GB): back to the device, not torch's cache
         finally:
             mmc.mmc_destroy(c16)
         h["net"] = mmc.mmc_net_create(ctx, weights)
