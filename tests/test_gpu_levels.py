@@ -136,6 +136,31 @@ def test_solve_refined(mmc, lat, sched):
         mmc.mmc_set_solve_refinement(lat.ctx, 3e-2, 8)
 
 
+@pytest.mark.parametrize("minb", [3, 6])
+def test_solve_8rhs_fourth_form(mmc, lat, minb):
+    """Refined solves of 8 vectors (the 8-rhs block class: Horner preconditioner chains
+    with the aux operand, M) through the fourth kernel form, with each link loaded whole
+    by every lane (minb 3) or in pieces exchanged by warp shuffles (minb 6): residual
+    1e-10 checked with the oracle's M."""
+    nrhs = 8
+    v = {"version": 4, "rpt": 1, "minb": minb, "spc": 64, "blocked": 0, "ns": 0}
+    mmc.mmc_set_step_variant_class(lat.ctx, mmc.MMC_F32, 0, v)
+    try:
+        b = mmc.new_field(lat.ctx, nrhs, 0)
+        x = mmc.new_field(lat.ctx, nrhs, 0)
+        mmc.mmc_noise(lat.ctx, 7, 0, mmc.MMC_TAG_NOISE, nrhs, 0, b)
+        hp, _ = mmc.mmc_gmres_poly(lat.ctx, 6)
+        its, rel = mmc.mmc_solve(lat.ctx, b, x, nrhs, 1e-10, hp, mmc.MMC_F32, 8, 200)
+        xs = mmc.mmc_unpack(lat.ctx, x, nrhs, 0, lat.V)
+        for j in range(nrhs):
+            e = lat.eta(j, 7)
+            r = np.linalg.norm(e - lat.op(xs[j])) / np.linalg.norm(e)
+            assert r <= 1.05e-10, (j, r)
+    finally:
+        mmc.mmc_set_step_variant_class(lat.ctx, mmc.MMC_F32, 0, {"version": 2, "rpt": 1, "minb": 4, "spc": 64,
+                                                                 "blocked": 0, "ns": 0})
+
+
 @pytest.mark.parametrize("prec,inner", [(0, 1), (1, 1), (1, 2)])
 def test_level_inverse_vs_dense(mmc, prec, inner):
     """Tr(M^-1 - p) samples on the 4^4 plain workload (eps 0.5, kappa 0.12) vs a dense solve:
