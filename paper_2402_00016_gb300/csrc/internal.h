@@ -419,7 +419,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       if (!done && ver_run == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e4 = cudaSuccess;
         const int mbr = ctx->var_minb[run.prec][rc];
-        const int mb = (mbr == 3 || mbr == 5 || mbr == 6) ? mbr : 4;
+        const int mb = mbr == 3 ? 3 : (mbr == 5 ? 5 : 4);
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
         done = run.prec == MMC_F32 ? mmc::launch_step4_f32(g.R, mb, p, nrb_k, nbx, s, &e4)
                                    : mmc::launch_step4_bf16(g.R, mb, p, nrb_k, nbx, s, &e4);

@@ -27,8 +27,8 @@ bool launch_step2_f32(int R, int rpt, int minb, const step_params& p, int n_rb, 
 bool launch_step2_bf16(int R, int rpt, int minb, const step_params& p, int n_rb, cudaStream_t s, cudaError_t* err);
 // Fourth form (stencil4.cuh): persistent grid over (rhs block, site pass) items with a
 // compact front, loads of the next hop issued before the current hop's products; one
-// rhs per lane, R = 8 or 16; minb 3 (168 registers), 4 (128), 5 (128, the links of
-// each pass staged in shared memory) or 6 (R = 8: 168, links exchanged by warp shuffles).  nbx: rows of the
+// rhs per lane, R = 8 or 16; minb 3 (168 registers), 4 (128) or 5 (128, the links of
+// each pass staged in shared memory).  nbx: rows of the
 // bilinear partials.  Returns false when the flags need another form.
 bool launch_step4_f32(int R, int minb, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err);
 bool launch_step4_bf16(int R, int minb, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err);

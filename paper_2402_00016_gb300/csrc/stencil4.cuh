@@ -18,12 +18,6 @@
 // Optionally (p.hint & 1) the result is stored with an L2 evict-first policy: it is
 // not read again by this launch, so L2 keeps the inputs instead.
 //
-// Shuffled links (SH, with 3 resident CTAs per SM): the first five lanes of a site load one
-// 16-byte piece each of the next hop's link and the site's lanes exchange them with warp
-// shuffles, instead of every lane loading the whole link: with 8-rhs blocks (four sites a
-// warp) a link load touches four sites' links, and the L1 data pipe, not DRAM, bounds the
-// launch.
-//
 // Link staging (SL, with 4 resident CTAs per SM): the eight links of each
 // site of an item are copied into shared memory (cp.async, 16-byte pieces, issued by the
 // site's own lanes at the start of the item, together with the first hop's spinor
@@ -183,37 +177,15 @@ __device__ __forceinline__ void load_link_shared(const float4* p, Link<float>& L
   L.u[8] = cmake(v.x, v.y);
 }
 
-// This lane's 16-byte piece (lane < 5 of its site) of the link (site, mu), zero otherwise.
-__device__ __forceinline__ float4 load_link_piece(const void* links, int site, int mu, int lane) {
-  if (lane >= 5) return make_float4(0.f, 0.f, 0.f, 0.f);
-  const uint4 raw = ldv4(reinterpret_cast<const float4*>(links) + (size_t(site) * 4 + mu) * 5 + lane);
-  return *reinterpret_cast<const float4*>(&raw);
-}
-
-// The whole link from the pieces held by lanes base..base+4 of the site (mask: its lanes).
-__device__ __forceinline__ void expand_link(const float4& q, int base, unsigned mask, Link<float>& L) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float a = __shfl_sync(mask, q.x, base + k), b = __shfl_sync(mask, q.y, base + k);
-    const float c = __shfl_sync(mask, q.z, base + k), d = __shfl_sync(mask, q.w, base + k);
-    L.u[2 * k] = cmake(a, b);
-    L.u[2 * k + 1] = cmake(c, d);
-  }
-  const float a = __shfl_sync(mask, q.x, base + 4), b = __shfl_sync(mask, q.y, base + 4);
-  L.u[8] = cmake(a, b);
-}
-
 // Hop D of the eight (0: x+, 1: x-, 2: y+, ..., 7: t-): project the spinor in `sp`,
 // start the loads of hop D+1 (or, after the last hop, of the own site) into `sp`
 // and `lk`, then multiply with the link of hop D and accumulate.
 // LATE: load the next link after the products (18 registers fewer, its latency not hidden).
 // SL: the link of hop D comes from this site's staged links `sl` (8 x 5 pieces).
-// SH: `lq` holds this lane's piece of hop D's link; the next hop's piece is loaded into it.
-template <typename S, int R, int RPT, int KD, int D, bool LATE, bool SL, bool SH>
+template <typename S, int R, int RPT, int KD, int D, bool LATE, bool SL>
 __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in, int site, const int4& nf,
                                               const int4& nb, cx<typename StoreTraits<S>::R> (&sp)[12][RPT],
-                                              Link<typename StoreTraits<S>::R>& lk, const float4* sl, float4& lq,
-                                              int lane, int base, unsigned mask,
+                                              Link<typename StoreTraits<S>::R>& lk, const float4* sl,
                                               cx<typename StoreTraits<S>::R> (&acc)[12][RPT]) {
   using T = typename StoreTraits<S>::R;
   constexpr int MU = D / 2;
@@ -227,14 +199,7 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
   const int nsite = D == 7 ? site
                            : NBWD ? (NMU == 0 ? nb.x : NMU == 1 ? nb.y : NMU == 2 ? nb.z : nb.w)
                                   : (NMU == 0 ? nf.x : NMU == 1 ? nf.y : NMU == 2 ? nf.z : nf.w);
-  if constexpr (SH) {
-    Link<T> lc;
-    expand_link(lq, base, mask, lc);
-    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
-    if constexpr (D < 7) lq = load_link_piece(p.links, NBWD ? nsite : site, NMU, lane);
-    multiply_add<T, RPT, MU, BWD, SG>(lc, h0, h1, acc);
-    fence_arr<T, RPT>(acc);
-  } else if constexpr (SL) {
+  if constexpr (SL) {
     Link<T> lc;
     load_link_shared(sl + D * 5, lc);
     load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
@@ -256,7 +221,7 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
 
 // TH: the insertion Theta of the code bilinear when fixed at compile time (0: the
 // identity), -1 when read from p.theta.
-template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH, bool SL, bool SH>
+template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH, bool SL>
 __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_chunks, int n_items) {
   using T = float;
   constexpr int L = R / RPT;    // lanes per site
@@ -372,25 +337,21 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
       }
     }
     load_spinor<S, R, RPT>(in + size_t(nf.x) * 12 * R, sp);
-    const int lbase = int(threadIdx.x & 31) / L * L;  // the site's first lane in the warp
-    float4 lq = make_float4(0.f, 0.f, 0.f, 0.f);
     if constexpr (SL) {
       cp_commit_wait_all();
       __syncwarp(site_mask);
-    } else if constexpr (SH) {
-      lq = load_link_piece(p.links, site, 0, lane);
     } else {
       load_link(p.links, site, 0, lk);
     }
     constexpr bool LT = (MINB >= 4) && !SL;
-    hop_pipelined<S, R, RPT, KD, 0, LT, SL, SH>(p, in, site, nf, nb, sp, lk, sl, lq, lane, lbase, site_mask, acc);
-    hop_pipelined<S, R, RPT, KD, 1, LT, SL, SH>(p, in, site, nf, nb, sp, lk, sl, lq, lane, lbase, site_mask, acc);
-    hop_pipelined<S, R, RPT, KD, 2, LT, SL, SH>(p, in, site, nf, nb, sp, lk, sl, lq, lane, lbase, site_mask, acc);
-    hop_pipelined<S, R, RPT, KD, 3, LT, SL, SH>(p, in, site, nf, nb, sp, lk, sl, lq, lane, lbase, site_mask, acc);
-    hop_pipelined<S, R, RPT, KD, 4, LT, SL, SH>(p, in, site, nf, nb, sp, lk, sl, lq, lane, lbase, site_mask, acc);
-    hop_pipelined<S, R, RPT, KD, 5, LT, SL, SH>(p, in, site, nf, nb, sp, lk, sl, lq, lane, lbase, site_mask, acc);
-    hop_pipelined<S, R, RPT, KD, 6, LT, SL, SH>(p, in, site, nf, nb, sp, lk, sl, lq, lane, lbase, site_mask, acc);
-    hop_pipelined<S, R, RPT, KD, 7, LT, SL, SH>(p, in, site, nf, nb, sp, lk, sl, lq, lane, lbase, site_mask, acc);  // leaves the own spinor in sp
+    hop_pipelined<S, R, RPT, KD, 0, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 1, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 2, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 3, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 4, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 5, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 6, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 7, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);  // leaves the own spinor in sp
 
     const size_t boff = rb_off + size_t(site) * 12 * R + r0;
     cx<T> si[RPT], so[RPT];
@@ -492,7 +453,7 @@ inline int resident_ctas(K kern) {
 
 // Dispatch of one (S, R) family over the epilogue modes (one rhs per lane); false
 // when the flags need another form.  nbx: rows of the bilinear partials (grid bound).
-template <typename S, int R, int MINB, bool SL, bool SH>
+template <typename S, int R, int MINB, bool SL>
 bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err) {
   constexpr int RPT = 1;
   const int f = p.flags;
@@ -505,23 +466,23 @@ bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_
   if ((f & SF_DAGGER) && (aux || acc != ACC_NONE)) return false;
   void (*kern)(step_params, int, int) = nullptr;
   if (f & SF_DAGGER) {
-    kern = step4_kernel<S, R, RPT, MINB, -1, false, ACC_NONE, -1, SL, SH>;
+    kern = step4_kernel<S, R, RPT, MINB, -1, false, ACC_NONE, -1, SL>;
   } else if (!aux) {
     switch (acc) {
-      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_NONE, -1, SL, SH>; break;
+      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_NONE, -1, SL>; break;
       case ACC_CODES:
-        kern = p.theta == 0 ? step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, 0, SL, SH>
-                            : step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, -1, SL, SH>;
+        kern = p.theta == 0 ? step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, 0, SL>
+                            : step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, -1, SL>;
         break;
-      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_Y, -1, SL, SH>; break;
-      default: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_LEFT, -1, SL, SH>; break;
+      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_Y, -1, SL>; break;
+      default: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_LEFT, -1, SL>; break;
     }
   } else {
     switch (acc) {
-      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_NONE, -1, SL, SH>; break;
-      case ACC_CODES: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_CODES, -1, SL, SH>; break;
-      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_Y, -1, SL, SH>; break;
-      default: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_LEFT, -1, SL, SH>; break;
+      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_NONE, -1, SL>; break;
+      case ACC_CODES: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_CODES, -1, SL>; break;
+      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_Y, -1, SL>; break;
+      default: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_LEFT, -1, SL>; break;
     }
   }
   constexpr int SPP = 128 / (R / RPT);
