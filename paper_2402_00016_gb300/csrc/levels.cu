@@ -676,6 +676,12 @@ int finish_level(mmc_ctx* ctx, int hi, int lo, int theta_op, int deflate, int n_
       if (new_dots) CK(cudaMemcpyAsync(dd.data(), tdots, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (herr == 2) {
+        // a bulk copy may still have been in flight when its CTA exited
+        ctx->failed = true;
+        RET(MMC_ERR_TIMEOUT, "mmc_trace_level: tensor-core projection gave up with copies in flight; "
+                             "the context is retired (destroy it)");
+      }
       if (herr) RET(MMC_ERR_TIMEOUT, "mmc_trace_level: tensor-core projection wait timed out");
       A.assign(size_t(k) * g.npad, cd(0, 0));
       B.assign(size_t(k) * g.npad, cd(0, 0));
