@@ -92,6 +92,11 @@ __device__ __forceinline__ float2 getc<__nv_bfloat162>(const __nv_bfloat162* f, 
   return __bfloat1622float2(f[i]);
 }
 
+// store in the field's own precision from its arithmetic type (no FP64 round trip)
+__device__ __forceinline__ void putc(double2* f, size_t i, double2 v) { f[i] = v; }
+__device__ __forceinline__ void putc(float2* f, size_t i, float2 v) { f[i] = v; }
+__device__ __forceinline__ void putc(__nv_bfloat162* f, size_t i, float2 v) { f[i] = __float22bfloat162_rn(v); }
+
 __device__ __forceinline__ size_t fidx(const geom& g, int rb, int site, int c, int r) {
   return ((size_t(rb) * g.V + site) * 12 + c) * g.R + r;
 }
@@ -398,13 +403,17 @@ __global__ void normalise_kernel(geom g, const T* src, const double2* nrm2, T* d
   const int r = threadIdx.x % g.R;
   const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
   if (site >= g.V) return;
-  double n2 = nrm2[rb * g.R + r].x;
-  double sc = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+  using R = typename Arith<T>::R;
+  using C = typename Arith<T>::C;
+  const double n2 = nrm2[rb * g.R + r].x;
+  const R sc = R(n2 > 0 ? 1.0 / sqrt(n2) : 0.0);  // in the field's arithmetic precision
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
     size_t e = fidx(g, rb, site, c, r);
-    double2 v = get<T>(src, e);
-    put<T>(dst, e, v.x * sc, v.y * sc);
+    C v = getc<T>(src, e);
+    v.x *= sc;
+    v.y *= sc;
+    putc(dst, e, v);
   }
 }
 
@@ -415,15 +424,20 @@ __global__ void axpby_kernel(geom g, const double2* a, const T* x, const double2
   const int site = (blockIdx.x * blockDim.x + threadIdx.x) / g.R;
   if (site >= g.V) return;
   const int rg = rb * g.R + r;
-  double2 ca = a ? a[rg] : make_double2(0, 0), cb = b ? b[rg] : make_double2(0, 0);
+  // in the field's arithmetic precision (FP32 for FP32 and BF16 fields)
+  using R = typename Arith<T>::R;
+  using C = typename Arith<T>::C;
+  const double2 da = a ? a[rg] : make_double2(0, 0), db = b ? b[rg] : make_double2(0, 0);
+  const R ax = R(da.x), ay = R(da.y), bx = R(db.x), by = R(db.y);
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
     size_t e = fidx(g, rb, site, c, r);
-    double2 xv = x ? get<T>(x, e) : make_double2(0, 0);
-    double2 yv = b ? get<T>(y, e) : make_double2(0, 0);
-    double re = ca.x * xv.x - ca.y * xv.y + cb.x * yv.x - cb.y * yv.y;
-    double im = ca.x * xv.y + ca.y * xv.x + cb.x * yv.y + cb.y * yv.x;
-    put<T>(y, e, re, im);
+    C xv = x ? getc<T>(x, e) : C{R(0), R(0)};
+    C yv = b ? getc<T>(y, e) : C{R(0), R(0)};
+    C o;
+    o.x = ax * xv.x - ay * xv.y + bx * yv.x - by * yv.y;
+    o.y = ax * xv.y + ay * xv.x + bx * yv.y + by * yv.x;
+    putc(y, e, o);
   }
 }
 
