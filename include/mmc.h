@@ -433,6 +433,13 @@ int mmc_set_solve_params(mmc_ctx* ctx, int m_inner, int max_outer);
  * falling by 10% a cycle.  inner_cycles = 1 returns to FP64 after every cycle.
  * Defaults 3e-2 and 8.  MMC_ERR_ARG outside 1..64 cycles or (0, 1]. */
 int mmc_set_solve_refinement(mmc_ctx* ctx, double inner_reduction, int inner_cycles);
+/* Gram-Schmidt passes of the Arnoldi process in the FP32/BF16 stage of the refined
+ * solves: 1 (classical Gram-Schmidt once, the default: the FP64 residual of the
+ * refinement corrects what a less orthogonal basis leaves, and on the 24^4 workload
+ * the matvecs are the same as with 2) or 2 (twice).  The Arnoldi runs of
+ * mmc_gmres_poly, mmc_deflate and the plain FP64 form always take 2.  MMC_ERR_ARG
+ * for other values. */
+int mmc_set_gram_schmidt(mmc_ctx* ctx, int passes);
 /* Storage of the inner FGMRES stage (its preconditioner chain included) in the
  * solves of the M^-1 level of a reduced-precision mmc_trace_level (Sec. 1,
  * Sec. 8; the prec_inner of mmc_solve): MMC_F32 (default) or MMC_BF16.  The FP64

@@ -275,6 +275,13 @@ int mmc_set_solve_refinement(mmc_ctx* ctx, double inner_reduction, int inner_cyc
   return MMC_OK;
 }
 
+int mmc_set_gram_schmidt(mmc_ctx* ctx, int passes) {
+  if (!ctx) return MMC_ERR_ARG;
+  if (passes != 1 && passes != 2) RET(MMC_ERR_ARG, "mmc_set_gram_schmidt: 1 or 2 passes");
+  ctx->solve_gs = passes;
+  return MMC_OK;
+}
+
 int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters) {
   if (!ctx || wait_iters < 0) return MMC_ERR_ARG;
   ctx->stall_test = enable != 0;

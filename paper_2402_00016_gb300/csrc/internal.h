@@ -96,6 +96,7 @@ struct mmc_ctx {
   double defl_max_u = 100.0;  // mmc_deflate: bound on the norm of a left vector u_i (a column of (W^H Z)^{-H})
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
+  int solve_gs = 1;          // Gram-Schmidt passes of the FP32 stage's Arnoldi (1 or 2)
   double solve_red = 3e-2;   // FP32 stage of the refined solves: gain per FP64 residual
   int solve_cycles = 8;      // and its most FGMRES cycles
   long long wait_iters = 0;   // bound of the staged kernel's mbarrier waits (0: its default)
@@ -821,8 +822,10 @@ struct ArnoldiOut {
   std::vector<double> beta;
 };
 
+// passes: 2 (classical Gram-Schmidt twice, the default) or 1 (once; FP32 bases only).
 template <class Op>
-inline int arnoldi_cgs2(mmc_ctx* ctx, const geom& g, int prec, void* V, int m, Op op, ArnoldiOut& out, cudaStream_t s) {
+inline int arnoldi_cgs2(mmc_ctx* ctx, const geom& g, int prec, void* V, int m, Op op, ArnoldiOut& out, cudaStream_t s,
+                        int passes = 2) {
   const size_t stride = size_t(g.npad) * g.V * 12;  // elements per basis field
   const size_t eb = elem_bytes(prec);
   const int spc = 256;
@@ -847,7 +850,12 @@ inline int arnoldi_cgs2(mmc_ctx* ctx, const geom& g, int prec, void* V, int m, O
     double2* hc = reinterpret_cast<double2*>(hcols) + size_t(j) * (m + 1) * g.npad;
     CK(mmc::launch_multidot(prec, g, V, stride, j + 1, W, 0, spc, (double2*)part, s));
     CK(mmc::launch_reduce((double2*)part, nbx, j + 1, g.npad, (double2*)h1, 0, s));
-    if (prec == MMC_F32 && j + 1 <= 8) {
+    if (prec == MMC_F32 && j + 1 <= 8 && passes == 1) {
+      // one pass: the update fused with the norm; the Hessenberg column is h1
+      CK(mmc::launch_update_dot(g, (const float2*)V, stride, j + 1, (double2*)h1, (float2*)W, true, spc,
+                                (double2*)part, s));
+      CK(cudaMemcpyAsync(hc, h1, size_t(j + 1) * g.npad * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    } else if (prec == MMC_F32 && j + 1 <= 8) {
       // FP32 basis: each update fused with the dot products that follow it (the second
       // pass's projections, then the norm), one read of the basis and of w each
       CK(mmc::launch_update_dot(g, (const float2*)V, stride, j + 1, (double2*)h1, (float2*)W, false, spc,

@@ -184,7 +184,7 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
   };
   auto cycle = [&]() -> int {
     ArnoldiOut ao;
-    TRY(arnoldi_cgs2(ctx, g, ip, Vb, m, op, ao, s));
+    TRY(arnoldi_cgs2(ctx, g, ip, Vb, m, op, ao, s, ip == MMC_F32 ? ctx->solve_gs : 2));
     inner += m;
     std::vector<cd> ycoef(size_t(m) * g.npad, cd(0, 0));
     for (int rr = 0; rr < g.npad; ++rr) {

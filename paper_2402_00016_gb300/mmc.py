@@ -131,6 +131,7 @@ _SIGS = {
     "mmc_graph_note": (ctypes.c_char_p, [_vp]),
     "mmc_set_solve_params": (_i, [_vp, _i, _i]),
     "mmc_set_solve_refinement": (_i, [_vp, _d, _i]),
+    "mmc_set_gram_schmidt": (_i, [_vp, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
     "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
     "mmc_leja_order": (_i, [_i, _dp, _dp]),
@@ -463,6 +464,10 @@ def mmc_set_solve_params(ctx, m_inner=0, max_outer=0):
 
 def mmc_set_solve_refinement(ctx, inner_reduction, inner_cycles):
     _check(lib.mmc_set_solve_refinement(ctx, float(inner_reduction), int(inner_cycles)), ctx)
+
+
+def mmc_set_gram_schmidt(ctx, passes):
+    _check(lib.mmc_set_gram_schmidt(ctx, int(passes)), ctx)
 
 
 def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):

@@ -136,6 +136,30 @@ def test_solve_refined(mmc, lat, sched):
         mmc.mmc_set_solve_refinement(lat.ctx, 3e-2, 8)
 
 
+@pytest.mark.parametrize("passes", [1, 2])
+def test_solve_gram_schmidt_passes(mmc, lat, passes):
+    """The FP32 stage with one (the default) or two Gram-Schmidt passes per Arnoldi step
+    reaches the 1e-10 residual (checked with the oracle's M); 1 and 2 are the only pass
+    counts."""
+    nrhs = 8
+    b = mmc.new_field(lat.ctx, nrhs, 0)
+    x = mmc.new_field(lat.ctx, nrhs, 0)
+    mmc.mmc_noise(lat.ctx, 8, 0, mmc.MMC_TAG_NOISE, nrhs, 0, b)
+    hp, _ = mmc.mmc_gmres_poly(lat.ctx, 6)
+    mmc.mmc_set_gram_schmidt(lat.ctx, passes)
+    try:
+        its, rel = mmc.mmc_solve(lat.ctx, b, x, nrhs, 1e-10, hp, mmc.MMC_F32, 8, 200)
+        xs = mmc.mmc_unpack(lat.ctx, x, nrhs, 0, lat.V)
+        for j in range(nrhs):
+            e = lat.eta(j, 8)
+            assert np.linalg.norm(e - lat.op(xs[j])) <= 1.05e-10 * np.linalg.norm(e), j
+        for bad in (0, 3):
+            with pytest.raises(mmc.MMCError):
+                mmc.mmc_set_gram_schmidt(lat.ctx, bad)
+    finally:
+        mmc.mmc_set_gram_schmidt(lat.ctx, 1)
+
+
 @pytest.mark.parametrize("minb", [3, 5])
 def test_solve_8rhs_fourth_form(mmc, lat, minb):
     """Refined solves of 8 vectors (the 8-rhs block class: Horner preconditioner chains
