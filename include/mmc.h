@@ -359,8 +359,8 @@ int mmc_probe_colouring(const int dims[4], int reach, int* colour, int* n_colour
 int mmc_net_create(mmc_ctx* ctx, const double* weights, uint64_t seed, int* handle);
 int mmc_net_set_weights(mmc_ctx* ctx, int handle, const double* weights);
 int mmc_net_get_weights(mmc_ctx* ctx, int handle, double* weights);
-/* Storage of the network's weights and hidden activations (spec precision
- * form): MMC_F32 (default) or MMC_BF16 (weights rounded to BF16 from the FP64
+/* Storage of the network's weights and hidden activations (the reduced-precision
+ * form; not in the paper): MMC_F32 (default) or MMC_BF16 (weights rounded to BF16 from the FP64
  * master copy, the 24-component hidden activations stored in BF16; FP32
  * arithmetic and accumulation; the input and output fields stay MMC_F32).  Both
  * inference and training use it; training keeps FP64 master weights (Adam on the
@@ -448,7 +448,7 @@ int mmc_set_gram_schmidt(mmc_ctx* ctx, int passes);
  * iteration tolerates the less accurate preconditioner at the cost of more
  * iterations.  MMC_ERR_ARG for any other value. */
 int mmc_set_solve_storage(mmc_ctx* ctx, int prec_inner);
-/* Rounding of BF16 chain storage (spec precision form; not in the paper):
+/* Rounding of BF16 chain storage (the reduced-precision form; not in the paper):
  * mode 0 rounds every stored element to nearest (default); mode 1 rounds it up or
  * down with probability given by its discarded bits, with random bits from a
  * counter-based hash of (element, step, a per-chain salt held in device memory and
