@@ -183,6 +183,19 @@ int mmc_load_gauge(mmc_ctx* ctx, const double* U, double kappa, int t_antiperiod
   if (!ctx->links32) CK(cudaMalloc(&ctx->links32, h32.size() * sizeof(float2)));
   CK(cudaMemcpy(ctx->links64, h64.data(), h64.size() * sizeof(double2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->links32, h32.data(), h32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  {
+    // special unitary links (third row = conjugate cross product of the first two, to
+    // 1e-10): the step-kernel form that rebuilds third rows may then run
+    void* flag;
+    TRY(scratch(ctx, "su3_flag", sizeof(int), &flag));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    CK(mmc::launch_su3_rows_check((const double2*)ctx->links64, V, slice, ctx->dims[3], t_antiperiodic ? 1 : 0,
+                                  (int*)flag, ctx->stream));
+    int bad = 1;
+    CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->links_su3 = bad == 0;
+  }
   ctx->kappa = kappa;
   ctx->tap = t_antiperiodic ? 1 : 0;
   ctx->gauge = true;
@@ -505,9 +518,11 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
       }
     }
     // the persistent, pipelined form (version 4, one rhs per lane): register caps (3: 168
-    // registers; 4: 128; 5: 128 with the links staged in shared memory) and traversals
+    // registers; 4: 128; 5: 128 with the links staged in shared memory; 6, 8-rhs blocks of
+    // special unitary links: 168 with each link's third row rebuilt) and traversals
     for (int ordr = 0; ordr <= 2; ++ordr)
-    for (int mb = 3; mb <= 5; ++mb) {
+    for (int mb = 3; mb <= 6; ++mb) {
+      if (mb == 6 && !(g.R == 8 && ctx->links_su3)) continue;
       if ((ordr == 1 && !ctx->order) || (ordr == 2 && !ctx->order_zh)) continue;
       ctx->var_ver[prec][rc] = 4;
       ctx->var_rpt[prec][rc] = 1;

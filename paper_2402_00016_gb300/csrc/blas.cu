@@ -839,6 +839,37 @@ cudaError_t launch_normalise(int prec, geom g, const void* src, const double2* n
   return cudaGetLastError();
 }
 
+// flag <- 1 if some FP64 link's third row differs by more than 1e-10 from the conjugate
+// cross product of its first two rows (negated on the time links at t = Lt - 1 when the
+// antiperiodic phase is folded in): the condition for rebuilding the third row.
+__global__ void su3_rows_check_kernel(const double2* __restrict__ links, int V, int slice, int Lt, int tap,
+                                      int* flag) {
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // link (site, mu)
+  if (l >= 4ll * V) return;
+  const int site = int(l / 4), mu = int(l % 4);
+  const double2* u = links + l * 9;
+  const double sg = (tap && mu == 3 && site >= (Lt - 1) * slice) ? -1.0 : 1.0;
+  bool bad = false;
+  for (int c = 0; c < 3; ++c) {
+    const int a = (c + 1) % 3, b = (c + 2) % 3;
+    const double2 x0 = u[a], y1 = u[3 + b], x1 = u[b], y0 = u[3 + a];
+    // (row0 x row1)_c = r0[a] r1[b] - r0[b] r1[a], then conjugated and signed
+    const double re = (x0.x * y1.x - x0.y * y1.y) - (x1.x * y0.x - x1.y * y0.y);
+    const double im = (x0.x * y1.y + x0.y * y1.x) - (x1.x * y0.y + x1.y * y0.x);
+    const double2 r2 = u[6 + c];
+    if (fabs(sg * re - r2.x) > 1e-10 || fabs(-sg * im - r2.y) > 1e-10) bad = true;
+  }
+  if (bad) atomicOr(flag, 1);
+}
+
+cudaError_t launch_su3_rows_check(const double2* links, int V, int slice, int Lt, int tap, int* flag,
+                                  cudaStream_t s) {
+  const long long n = 4ll * V;
+  su3_rows_check_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(links, V, slice, Lt, tap, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_update_dot(geom g, const float2* A, size_t a_stride, int nvec, const double2* h, float2* w,
                               bool norm, int spc, double2* partial, cudaStream_t s) {
   if (nvec < 1 || nvec > 8) return cudaErrorInvalidValue;

@@ -57,6 +57,7 @@ struct mmc_ctx {
   bool gauge = false;
   void* links64 = nullptr;
   void* links32 = nullptr;
+  bool links_su3 = false;  // every link special unitary (to 1e-10): a link's third row follows from two
   std::vector<mmc::host::Poly> polys;
   std::vector<mmc::host::Net> nets;
   // deflation data (FP64 single-vector fields [site][12])
@@ -420,7 +421,8 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
       if (!done && ver_run == 4 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e4 = cudaSuccess;
         const int mbr = ctx->var_minb[run.prec][rc];
-        const int mb = mbr == 3 ? 3 : (mbr == 5 ? 5 : 4);
+        // 6 (rebuilt third link rows) needs special unitary links, else the 168-register form
+        const int mb = mbr == 3 ? 3 : mbr == 5 ? 5 : mbr == 6 ? (ctx->links_su3 && g.R == 8 ? 6 : 3) : 4;
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
         done = run.prec == MMC_F32 ? mmc::launch_step4_f32(g.R, mb, p, nrb_k, nbx, s, &e4)
                                    : mmc::launch_step4_bf16(g.R, mb, p, nrb_k, nbx, s, &e4);

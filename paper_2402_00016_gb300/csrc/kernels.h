@@ -79,6 +79,10 @@ cudaError_t launch_reduce(const double2* partial, int nbx, int nvec, int npad, d
 // w -= sum_i A_i * h[i][r] (h device, double2 [nvec][npad]).
 cudaError_t launch_basis_update(int prec, geom g, const void* A, size_t a_stride, int nvec, const double2* h,
                                 void* w, cudaStream_t s);
+// flag |= 1 when a FP64 link's third row is not the (phase-signed) conjugate cross
+// product of its first two to 1e-10.
+cudaError_t launch_su3_rows_check(const double2* links, int V, int slice, int Lt, int tap, int* flag,
+                                  cudaStream_t s);
 // FP32 fields: w <- w - sum_i h_i A_i (nvec <= 8), then per-CTA partials (rows of spc
 // sites, as launch_multidot) of A_i^H w (norm false, nvec rows) or of w^H w (norm true).
 cudaError_t launch_update_dot(geom g, const float2* A, size_t a_stride, int nvec, const double2* h, float2* w,

@@ -18,6 +18,12 @@
 // Optionally (p.hint & 1) the result is stored with an L2 evict-first policy: it is
 // not read again by this launch, so L2 keeps the inputs instead.
 //
+// Reconstructed links (RC, with 3 resident CTAs per SM, special unitary gauge fields
+// only): a hop loads the first two rows of its link (three 16-byte pieces instead of
+// five) and rebuilds the third as the complex conjugate of their cross product, negated
+// on the time links that carry the antiperiodic phase; with 8-rhs blocks the launch is
+// bound by the L1 data pipe, and the link loads are a third of its requests.
+//
 // Link staging (SL, with 4 resident CTAs per SM): the eight links of each
 // site of an item are copied into shared memory (cp.async, 16-byte pieces, issued by the
 // site's own lanes at the start of the item, together with the first hop's spinor
@@ -177,12 +183,38 @@ __device__ __forceinline__ void load_link_shared(const float4* p, Link<float>& L
   L.u[8] = cmake(v.x, v.y);
 }
 
+// The first two rows of the link (site, mu) (u[0..5]; u[6..8] are rebuilt by complete_link).
+__device__ __forceinline__ void load_link_rows(const void* links, int site, int mu, Link<float>& L) {
+  const float4* p = reinterpret_cast<const float4*>(links) + (size_t(site) * 4 + mu) * 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uint4 raw = ldv4(p + k);
+    float4 v = *reinterpret_cast<const float4*>(&raw);
+    L.u[2 * k] = cmake(v.x, v.y);
+    L.u[2 * k + 1] = cmake(v.z, v.w);
+  }
+}
+
+// Third row of a special unitary link from the first two: conj(row0 x row1), times -1
+// for a link that carries the antiperiodic phase (all of its rows were negated).
+__device__ __forceinline__ void complete_link(Link<float>& L, bool neg) {
+  const cx<float>*a = &L.u[0], *b = &L.u[3];
+  cx<float> c0 = csub(cmul(a[1], b[2]), cmul(a[2], b[1]));
+  cx<float> c1 = csub(cmul(a[2], b[0]), cmul(a[0], b[2]));
+  cx<float> c2 = csub(cmul(a[0], b[1]), cmul(a[1], b[0]));
+  const float sg = neg ? -1.f : 1.f;
+  L.u[6] = cmake(sg * c0.re, -sg * c0.im);
+  L.u[7] = cmake(sg * c1.re, -sg * c1.im);
+  L.u[8] = cmake(sg * c2.re, -sg * c2.im);
+}
+
 // Hop D of the eight (0: x+, 1: x-, 2: y+, ..., 7: t-): project the spinor in `sp`,
 // start the loads of hop D+1 (or, after the last hop, of the own site) into `sp`
 // and `lk`, then multiply with the link of hop D and accumulate.
 // LATE: load the next link after the products (18 registers fewer, its latency not hidden).
 // SL: the link of hop D comes from this site's staged links `sl` (8 x 5 pieces).
-template <typename S, int R, int RPT, int KD, int D, bool LATE, bool SL>
+// RC: `lk` holds the first two rows of hop D's link; the third is rebuilt here.
+template <typename S, int R, int RPT, int KD, int D, bool LATE, bool SL, bool RC>
 __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in, int site, const int4& nf,
                                               const int4& nb, cx<typename StoreTraits<S>::R> (&sp)[12][RPT],
                                               Link<typename StoreTraits<S>::R>& lk, const float4* sl,
@@ -210,6 +242,16 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
     multiply_add<T, RPT, MU, BWD, SG>(lk, h0, h1, acc);
     fence_arr<T, RPT>(acc);
     if constexpr (D < 7) load_link(p.links, NBWD ? nsite : site, NMU, lk);
+  } else if constexpr (RC) {
+    Link<T> lc = lk;
+    // the time link at t = Lt - 1 (forward from there, backward from t = 0) carries the phase
+    const int lsite = BWD ? (MU == 0 ? nb.x : MU == 1 ? nb.y : MU == 2 ? nb.z : nb.w) : site;
+    const bool neg = MU == 3 && p.tap && lsite >= (p.Lt - 1) * p.Lx * p.Ly * p.Lz;
+    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);
+    if constexpr (D < 7) load_link_rows(p.links, NBWD ? nsite : site, NMU, lk);
+    complete_link(lc, neg);
+    multiply_add<T, RPT, MU, BWD, SG>(lc, h0, h1, acc);
+    fence_arr<T, RPT>(acc);
   } else {
     const Link<T> lc = lk;
     load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);
@@ -221,7 +263,7 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
 
 // TH: the insertion Theta of the code bilinear when fixed at compile time (0: the
 // identity), -1 when read from p.theta.
-template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH, bool SL>
+template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH, bool SL, bool RC>
 __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_chunks, int n_items) {
   using T = float;
   constexpr int L = R / RPT;    // lanes per site
@@ -340,18 +382,20 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
     if constexpr (SL) {
       cp_commit_wait_all();
       __syncwarp(site_mask);
+    } else if constexpr (RC) {
+      load_link_rows(p.links, site, 0, lk);
     } else {
       load_link(p.links, site, 0, lk);
     }
     constexpr bool LT = (MINB >= 4) && !SL;
-    hop_pipelined<S, R, RPT, KD, 0, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 1, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 2, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 3, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 4, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 5, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 6, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 7, LT, SL>(p, in, site, nf, nb, sp, lk, sl, acc);  // leaves the own spinor in sp
+    hop_pipelined<S, R, RPT, KD, 0, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 1, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 2, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 3, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 4, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 5, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 6, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 7, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);  // leaves the own spinor in sp
 
     const size_t boff = rb_off + size_t(site) * 12 * R + r0;
     cx<T> si[RPT], so[RPT];
@@ -453,7 +497,7 @@ inline int resident_ctas(K kern) {
 
 // Dispatch of one (S, R) family over the epilogue modes (one rhs per lane); false
 // when the flags need another form.  nbx: rows of the bilinear partials (grid bound).
-template <typename S, int R, int MINB, bool SL>
+template <typename S, int R, int MINB, bool SL, bool RC>
 bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err) {
   constexpr int RPT = 1;
   const int f = p.flags;
@@ -466,23 +510,23 @@ bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_
   if ((f & SF_DAGGER) && (aux || acc != ACC_NONE)) return false;
   void (*kern)(step_params, int, int) = nullptr;
   if (f & SF_DAGGER) {
-    kern = step4_kernel<S, R, RPT, MINB, -1, false, ACC_NONE, -1, SL>;
+    kern = step4_kernel<S, R, RPT, MINB, -1, false, ACC_NONE, -1, SL, RC>;
   } else if (!aux) {
     switch (acc) {
-      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_NONE, -1, SL>; break;
+      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_NONE, -1, SL, RC>; break;
       case ACC_CODES:
-        kern = p.theta == 0 ? step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, 0, SL>
-                            : step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, -1, SL>;
+        kern = p.theta == 0 ? step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, 0, SL, RC>
+                            : step4_kernel<S, R, RPT, MINB, 1, false, ACC_CODES, -1, SL, RC>;
         break;
-      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_Y, -1, SL>; break;
-      default: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_LEFT, -1, SL>; break;
+      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_Y, -1, SL, RC>; break;
+      default: kern = step4_kernel<S, R, RPT, MINB, 1, false, ACC_LEFT, -1, SL, RC>; break;
     }
   } else {
     switch (acc) {
-      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_NONE, -1, SL>; break;
-      case ACC_CODES: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_CODES, -1, SL>; break;
-      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_Y, -1, SL>; break;
-      default: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_LEFT, -1, SL>; break;
+      case ACC_NONE: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_NONE, -1, SL, RC>; break;
+      case ACC_CODES: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_CODES, -1, SL, RC>; break;
+      case ACC_Y: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_Y, -1, SL, RC>; break;
+      default: kern = step4_kernel<S, R, RPT, MINB, 1, true, ACC_LEFT, -1, SL, RC>; break;
     }
   }
   constexpr int SPP = 128 / (R / RPT);
