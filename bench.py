@@ -123,6 +123,7 @@ TRAFFIC_PER_SITE_RHS = {
     (4, 3, 2, "bilinear", 1): (3.220147e9 + 2.017138e9) / (331776 * 64),  # 246.6 B
     # the Horner chains of the 8-rhs solves (one launch of the kernel_bench solve mode)
     (4, 3, 0, "aux", 1): (669.179392e6 + 238.431744e6) / (331776 * 8),  # 341.9 B
+    (4, 6, 0, "aux", 1): (671.003392e6 + 239.062528e6) / (331776 * 8),  # 342.9 B, third link rows rebuilt
 }
 
 
