@@ -494,7 +494,9 @@ int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters);
  * rhs per lane, a persistent grid whose CTAs take (rhs block, pass of sites)
  * items round-robin so that the sites in flight form one compact front, and
  * the loads of each hop issued while the previous hop computes (minb 3: 168
- * registers, 4: 128, 5: 128 with each pass's links staged in shared memory); 5: as 4 with
+ * registers, 4: 128, 5: 128 with each pass's links staged in shared memory, 6: 168 with
+ * each link's third row rebuilt from its first two, used when mmc_load_gauge found every
+ * link special unitary and as minb 3 otherwise); 5: as 4 with
  * the operands of the hops staged in shared memory by per-lane asynchronous
  * copies several hops ahead, the depth set by 300 + n, FP32 3 or 4 (default 4),
  * BF16 4 (default) or 6), or 200 + b

@@ -518,11 +518,11 @@ int mmc_autotune(mmc_ctx* ctx, int nrhs, int prec, int* best, double* ms_out) {
       }
     }
     // the persistent, pipelined form (version 4, one rhs per lane): register caps (3: 168
-    // registers; 4: 128; 5: 128 with the links staged in shared memory; 6, 8-rhs blocks of
-    // special unitary links: 168 with each link's third row rebuilt) and traversals
+    // registers; 4: 128; 5: 128 with the links staged in shared memory; 6, special unitary
+    // links: 168 with each link's third row rebuilt) and traversals
     for (int ordr = 0; ordr <= 2; ++ordr)
     for (int mb = 3; mb <= 6; ++mb) {
-      if (mb == 6 && !(g.R == 8 && ctx->links_su3)) continue;
+      if (mb == 6 && !ctx->links_su3) continue;
       if ((ordr == 1 && !ctx->order) || (ordr == 2 && !ctx->order_zh)) continue;
       ctx->var_ver[prec][rc] = 4;
       ctx->var_rpt[prec][rc] = 1;

@@ -422,7 +422,7 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
         cudaError_t e4 = cudaSuccess;
         const int mbr = ctx->var_minb[run.prec][rc];
         // 6 (rebuilt third link rows) needs special unitary links, else the 168-register form
-        const int mb = mbr == 3 ? 3 : mbr == 5 ? 5 : mbr == 6 ? (ctx->links_su3 && g.R == 8 ? 6 : 3) : 4;
+        const int mb = mbr == 3 ? 3 : mbr == 5 ? 5 : mbr == 6 ? (ctx->links_su3 ? 6 : 3) : 4;
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);
         done = run.prec == MMC_F32 ? mmc::launch_step4_f32(g.R, mb, p, nrb_k, nbx, s, &e4)
                                    : mmc::launch_step4_bf16(g.R, mb, p, nrb_k, nbx, s, &e4);

@@ -21,8 +21,9 @@
 // Reconstructed links (RC, with 3 resident CTAs per SM, special unitary gauge fields
 // only): a hop loads the first two rows of its link (three 16-byte pieces instead of
 // five) and rebuilds the third as the complex conjugate of their cross product, negated
-// on the time links that carry the antiperiodic phase; with 8-rhs blocks the launch is
-// bound by the L1 data pipe, and the link loads are a third of its requests.
+// on the time links that carry the antiperiodic phase.  With 8-rhs blocks the launch is
+// bound by the L1 data pipe, and the link loads are a third of its requests; with 16-rhs
+// blocks a link's loads are shared by twice the rhs.
 //
 // Link staging (SL, with 4 resident CTAs per SM): the eight links of each
 // site of an item are copied into shared memory (cp.async, 16-byte pieces, issued by the

@@ -3,9 +3,10 @@
 
 namespace mmc {
 bool launch_step4_f32(int R, int minb, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err) {
-  // minb 3: 168 registers; 4: 128; 5: 128 with the links staged in shared memory; 6 (8-rhs
-  // blocks, special unitary links): 168 with each link's third row rebuilt from the first two
+  // minb 3: 168 registers; 4: 128; 5: 128 with the links staged in shared memory; 6 (special
+  // unitary links): 168 with each link's third row rebuilt from the first two
   if (R == 16) return minb == 3 ? sten4::launch4<float2, 16, 3, false, false>(p, n_rb, nbx, s, err)
+                     : minb == 6 ? sten4::launch4<float2, 16, 3, false, true>(p, n_rb, nbx, s, err)
                      : minb == 5 ? sten4::launch4<float2, 16, 4, true, false>(p, n_rb, nbx, s, err)
                                  : sten4::launch4<float2, 16, 4, false, false>(p, n_rb, nbx, s, err);
   if (R == 8) return minb == 3 ? sten4::launch4<float2, 8, 3, false, false>(p, n_rb, nbx, s, err)

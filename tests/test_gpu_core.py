@@ -195,7 +195,7 @@ def test_step_kernel_variants(mmc, lat, prec, ver, rpt, minb, nrhs):
     """Every step-kernel version (generic, compile-time rhs block, rows staged by bulk
     copies with the deepest and the shallowest ring, one or two rhs per lane, the
     persistent pipelined form with either register cap, with its links staged in shared
-    memory or rebuilt from two rows (8-rhs blocks), and with evict-first stores, the
+    memory or rebuilt from two rows, and with evict-first stores, the
     form with operands staged by asynchronous copies at each pipeline depth), lane widths
     and register caps give M x, and M^+ x for the staged and persistent forms."""
     mmc.mmc_set_step_variant(lat.ctx, prec, rpt, 100 + ver, 0)
@@ -263,23 +263,23 @@ def test_step_variant_per_rhs_class(mmc, lat, prec):
 
 @pytest.mark.parametrize("prec", [1, 2])
 def test_rebuilt_link_rows_need_special_unitary_links(mmc, prec):
-    """The form that rebuilds each link's third row (minb 6, 8-rhs blocks) on a gauge field
-    with one link that is not special unitary: the library detects it at load time and
-    runs the form that loads whole links, so M x still matches the oracle; on the special
-    unitary field (antiperiodic time, the negated boundary links included) the rebuilt
-    rows match it too."""
+    """The form that rebuilds each link's third row (minb 6, 8- and 16-rhs blocks) on a
+    gauge field with one link that is not special unitary: the library detects it at load
+    time and runs the form that loads whole links, so M x still matches the oracle; on the
+    special unitary field (antiperiodic time, the negated boundary links included) the
+    rebuilt rows match it too."""
     dims = (4, 4, 2, 6)
     shape = (6, 2, 4, 4, 4, 3)
     U = synth.random_gauge(dims, 0.5, 4)
     bad = U.copy()
     bad[3, 5, 1, 2, 3] *= 1.25  # one time link at t = Lt - 1, scaled
-    nrhs = 6
-    for field in (U, bad):
+    for field, nrhs in ((U, 6), (bad, 6), (U, 21), (bad, 21)):
         ctx = mmc.mmc_create(dims, seed=3, device=0)
         try:
             mmc.mmc_load_gauge(ctx, field, 0.13, 1)
-            mmc.mmc_set_step_variant_class(ctx, prec, 0, {"version": 4, "rpt": 1, "minb": 6, "spc": 64,
-                                                          "blocked": 0, "ns": 0})
+            for rc in (0, 1):
+                mmc.mmc_set_step_variant_class(ctx, prec, rc, {"version": 4, "rpt": 1, "minb": 6, "spc": 64,
+                                                               "blocked": 0, "ns": 0})
             xs = synth.random_spinor(dims, 12, nrhs).transpose(6, 0, 1, 2, 3, 4, 5).reshape(nrhs, -1)
             x = mmc.new_field(ctx, nrhs, prec)
             y = mmc.new_field(ctx, nrhs, prec)
