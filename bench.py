@@ -121,6 +121,19 @@ TRAFFIC_PER_SITE_RHS = {
     # (kernel version, register cap, traversal, class kind, storage precision): bytes per site and rhs
     (2, 4, 1, "bilinear", 1): (4.671779e9 + 2.024867e9) / (331776 * 64),  # 315.4 B
     (4, 3, 2, "bilinear", 1): (3.220147e9 + 2.017138e9) / (331776 * 64),  # 246.6 B
+    # the other fourth-form variants (register cap 3..6, traversal 0..2), one capture of the
+    # eight launches of the timed level of each (their median)
+    (4, 3, 0, "bilinear", 1): (4.801522e9 + 2.017512e9) / (331776 * 64),  # 321.1 B
+    (4, 3, 1, "bilinear", 1): (4.842631e9 + 2.013644e9) / (331776 * 64),  # 322.9 B
+    (4, 4, 0, "bilinear", 1): (4.308748e9 + 2.018456e9) / (331776 * 64),  # 298.0 B
+    (4, 4, 1, "bilinear", 1): (4.840953e9 + 2.013706e9) / (331776 * 64),  # 322.8 B
+    (4, 4, 2, "bilinear", 1): (3.468966e9 + 2.014524e9) / (331776 * 64),  # 258.2 B
+    (4, 5, 0, "bilinear", 1): (4.598836e9 + 2.021913e9) / (331776 * 64),  # 311.8 B, links staged in shared memory
+    (4, 5, 1, "bilinear", 1): (4.829387e9 + 2.018181e9) / (331776 * 64),  # 322.5 B, links staged in shared memory
+    (4, 5, 2, "bilinear", 1): (3.576689e9 + 2.017936e9) / (331776 * 64),  # 263.5 B, links staged in shared memory
+    (4, 6, 0, "bilinear", 1): (4.484482e9 + 2.016758e9) / (331776 * 64),  # 306.2 B, third link rows rebuilt
+    (4, 6, 1, "bilinear", 1): (4.827532e9 + 2.014122e9) / (331776 * 64),  # 322.2 B, third link rows rebuilt
+    (4, 6, 2, "bilinear", 1): (3.473146e9 + 2.012985e9) / (331776 * 64),  # 258.4 B, third link rows rebuilt
     # the Horner chains of the 8-rhs solves (one launch of the kernel_bench solve mode)
     (4, 3, 0, "aux", 1): (669.179392e6 + 238.431744e6) / (331776 * 8),  # 341.9 B
     (4, 6, 0, "aux", 1): (671.003392e6 + 239.062528e6) / (331776 * 8),  # 342.9 B, third link rows rebuilt
