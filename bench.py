@@ -256,6 +256,9 @@ def main():
     ap.add_argument("--precond", default="in", choices=["in", "dbl"],
                     help="right preconditioner of those solves: the inner GMRES polynomial (degree 39) or the "
                          "double polynomial (degree 319)")
+    ap.add_argument("--horner-layout", default="paired", choices=["blocked", "paired"],
+                    help="layout of the Horner preconditioner chains in the 8-rhs solves (paired: two "
+                         "components of an rhs per 16-byte access, converted in and out per application)")
     ap.add_argument("--solve-storage", default="f32", choices=["f32", "bf16"],
                     help="storage of the inner FGMRES stage and its preconditioner chain in those solves (the "
                          "FP64 outer loop refines to 1e-10 either way)")
@@ -338,6 +341,7 @@ def main():
                          seed=W.noise_seed)
     mmc.mmc_set_solve_params(ctx, args.solve_m, 400)
     mmc.mmc_set_solve_storage(ctx, mmc.PREC[args.solve_storage])
+    mmc.mmc_set_horner_layout(ctx, 1 if args.horner_layout == "paired" else 0)
     t_poly = time.time() - t_setup
     lam = mmc.mmc_deflate(ctx, args.deflate_k, h["in"], args.arnoldi, 1e-3) if args.deflate_k > 0 else []
     if args.dbl_deflated:
@@ -543,7 +547,8 @@ def main():
                    "deflated": len(lam), "probe_colours": ncol,
                    "batch": "polynomial levels merged (one launch per degree)" if args.merged else "per level",
                    "solves": {"fgmres_m": args.solve_m, "precond": "p_in (degree 39)" if args.precond == "in"
-                              else "p_dbl (degree 319)", "tol": 1e-10, "inner_storage": args.solve_storage}, "l2": "inputs larger than L2 (GB-sized fields)",
+                              else "p_dbl (degree 319)", "tol": 1e-10, "inner_storage": args.solve_storage,
+                              "horner_layout": args.horner_layout}, "l2": "inputs larger than L2 (GB-sized fields)",
                    "parallelism": "replicas" if world > 1 else "1 gpu"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,

@@ -440,6 +440,17 @@ int mmc_set_solve_refinement(mmc_ctx* ctx, double inner_reduction, int inner_cyc
  * mmc_gmres_poly, mmc_deflate and the plain FP64 form always take 2.  MMC_ERR_ARG
  * for other values. */
 int mmc_set_gram_schmidt(mmc_ctx* ctx, int passes);
+/* Field layout of the Horner chains of the polynomial preconditioner (Sec. 8: FGMRES
+ * right-preconditioned by p_in) in the FP32 stage of 8-rhs solves: 0 keeps the blocked
+ * layout [site][c][rhs]; 1 moves the input into a paired-component layout
+ * [site][c/2][rhs][c%2] for the chain and the result back (two extra field passes per
+ * application), so that the step kernel's lanes load and store two components of
+ * their rhs in one 16-byte access and a site's 8 lanes read whole 128-byte lines.
+ * Used only where the 8-rhs FP32 variant is the fourth kernel form (at 168
+ * registers: minb 4 or 5 run as 3); the arithmetic is the same, so results are
+ * bit-identical to layout 0.  Default 1 (on the 24^4 workload 0.189 against 0.213 ms
+ * per Horner step).  MMC_ERR_ARG for other values. */
+int mmc_set_horner_layout(mmc_ctx* ctx, int paired);
 /* Storage of the inner FGMRES stage (its preconditioner chain included) in the
  * solves of the M^-1 level of a reduced-precision mmc_trace_level (Sec. 1,
  * Sec. 8; the prec_inner of mmc_solve): MMC_F32 (default) or MMC_BF16.  The FP64

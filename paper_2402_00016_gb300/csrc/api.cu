@@ -295,6 +295,13 @@ int mmc_set_gram_schmidt(mmc_ctx* ctx, int passes) {
   return MMC_OK;
 }
 
+int mmc_set_horner_layout(mmc_ctx* ctx, int paired) {
+  if (!ctx) return MMC_ERR_ARG;
+  if (paired != 0 && paired != 1) RET(MMC_ERR_ARG, "mmc_set_horner_layout: 0 or 1");
+  ctx->horner_paired = paired;
+  return MMC_OK;
+}
+
 int mmc_test_stall_staged(mmc_ctx* ctx, int enable, long long wait_iters) {
   if (!ctx || wait_iters < 0) return MMC_ERR_ARG;
   ctx->stall_test = enable != 0;

@@ -785,6 +785,31 @@ cudaError_t launch_salt_advance(uint32_t* salt, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// FP32 field between the blocked layout [rb][site][c][R] and the paired-component layout
+// [rb][site][c/2][R][c%2] (a permutation within each site's 12 R elements)
+__global__ void pair_layout_kernel(size_t n, int R, int to_paired, float2* __restrict__ dst,
+                                   const float2* __restrict__ src) {
+  const size_t blk_elems = size_t(12) * R;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    const size_t blk = i / blk_elems;
+    const int w = int(i - blk * blk_elems);
+    const int c = w / R, r = w - c * R;
+    const size_t j = blk * blk_elems + size_t(c >> 1) * 2 * R + 2 * r + (c & 1);
+    if (to_paired)
+      dst[j] = src[i];
+    else
+      dst[i] = src[j];
+  }
+}
+
+cudaError_t launch_pair_layout(void* dst, const void* src, geom g, int to_paired, cudaStream_t s) {
+  const size_t n = size_t(g.nrb) * g.V * 12 * g.R;
+  const unsigned blocks = unsigned(std::min<size_t>((n + 255) / 256, 152 * 64));
+  pair_layout_kernel<<<blocks, 256, 0, s>>>(n, g.R, to_paired, (float2*)dst, (const float2*)src);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert(int pd, void* dst, int ps, const void* src, geom g, cudaStream_t s) {
   size_t n = size_t(g.nrb) * g.V * 12 * g.R;
   if (pd == 0)

@@ -15,10 +15,12 @@ enum StepFlags : int {
   SF_BIL_CODES = 16, // bilinear with Z(4) noise given by packed codes
   SF_BIL_LEFT = 32,  // bilinear with an explicit left field
   SF_BIL_OUT = 64,   // bilinear also of `out` (weight w_out)
-  SF_DAGGER = 128    // use M^+ (gamma_mu signs flipped)
+  SF_DAGGER = 128,   // use M^+ (gamma_mu signs flipped)
+  SF_PAIRED = 256    // fields in the paired-component layout (fourth form, FP32, 8-rhs blocks)
 };
 
-// Per-step parameters.  Fields use the blocked layout [rb][site][c][R].
+// Per-step parameters.  Fields use the blocked layout [rb][site][c][R]; with SF_PAIRED
+// the components of a site pair up per rhs: [rb][site][c/2][R][c%2].
 struct step_params {
   const void* in;
   void* out;

@@ -98,6 +98,7 @@ struct mmc_ctx {
   int solve_m = 48;        // inner FGMRES length of the M^-1 level solves
   int solve_max_outer = 400;
   int solve_gs = 1;          // Gram-Schmidt passes of the FP32 stage's Arnoldi (1 or 2)
+  int horner_paired = 1;     // FP32 8-rhs Horner chains of the solves in the paired-component layout
   double solve_red = 3e-2;   // FP32 stage of the refined solves: gain per FP64 residual
   int solve_cycles = 8;      // and its most FGMRES cycles
   long long wait_iters = 0;   // bound of the staged kernel's mbarrier waits (0: its default)
@@ -410,7 +411,17 @@ inline int exec_run(mmc_ctx* ctx, Run& run, cudaStream_t s) {
         CK(cudaEventRecord(e0, s));
       }
       bool done = false;
-      if (ver_run == 5 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
+      if (p.flags & mmc::SF_PAIRED) {
+        // the paired-component layout exists in the fourth form only (FP32, 8-rhs blocks, 168
+        // registers); no other kernel reads it, so there is no fallback
+        cudaError_t e4 = cudaSuccess;
+        const int mb = (ctx->var_minb[run.prec][rc] == 6 && ctx->links_su3) ? 6 : 3;
+        if (run.prec != MMC_F32 || g.R != 8 || !mmc::launch_step4_f32(g.R, mb, p, nrb_k, 1 << 30, s, &e4))
+          RET(MMC_ERR_ARG, "exec_run: the paired-component layout needs FP32 8-rhs Horner steps");
+        CK(e4);
+        done = true;
+      }
+      if (!done && ver_run == 5 && run.prec != MMC_F64 && (g.R == 8 || g.R == 16)) {
         cudaError_t e5 = cudaSuccess;
         const int ns = ctx->var_ns[run.prec][rc];
         const int nbx = run.nbx > 0 ? run.nbx : (1 << 30);

@@ -67,6 +67,9 @@ cudaError_t launch_salt_advance(uint32_t* salt, cudaStream_t s);
 
 // dst (precision pd) = src (precision ps), same geometry.
 cudaError_t launch_convert(int pd, void* dst, int ps, const void* src, geom g, cudaStream_t s);
+// FP32 field dst = src moved into (to_paired = 1) or out of (0) the paired-component
+// layout of SF_PAIRED; dst and src distinct.
+cudaError_t launch_pair_layout(void* dst, const void* src, geom g, int to_paired, cudaStream_t s);
 
 // Per-rhs partial dots for a set of basis fields: partial[bx][i][npad] =
 // sum over the CTA's sites of conj(A_i) . w (optionally with Theta on w).

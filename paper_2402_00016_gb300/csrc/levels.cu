@@ -152,6 +152,10 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
                  ctx->polys[precond].theta.size() >= 2) {
         // single polynomial: Horner nesting, no accumulator field (3 field passes per degree)
         const int hp = prec_inner == MMC_BF16 ? MMC_BF16 : ip;
+        // the paired-component layout (one 16-byte access per two components of an rhs)
+        // for FP32 chains of 8-rhs blocks run by the fourth kernel form
+        const bool paired = ctx->horner_paired && hp == MMC_F32 && ip == MMC_F32 && g.R == 8 &&
+                            ctx->var_ver[MMC_F32][rclass(g.R)] == 4;
         void *Q0, *Q1, *src = const_cast<void*>(vj), *dst = zdst;
         TRY(scratch(ctx, "sv_h0", field_bytes(g, hp), &Q0));
         TRY(scratch(ctx, "sv_h1", field_bytes(g, hp), &Q1));
@@ -163,11 +167,21 @@ int solve_impl(mmc_ctx* ctx, const void* b, void* x, int nrhs, double tol, int p
           CK(mmc::launch_convert(hp, v16, ip, vj, g, s));
           src = v16;
           dst = o16;
+        } else if (paired) {
+          void *vp, *op;
+          TRY(scratch(ctx, "sv_vp", field_bytes(g, hp), &vp));
+          TRY(scratch(ctx, "sv_op", field_bytes(g, hp), &op));
+          CK(mmc::launch_pair_layout(vp, vj, g, 1, s));
+          src = vp;
+          dst = op;
         }
         base.prec = hp;
         build_horner(ctx, base, ctx->polys[precond].theta, src, Q0, Q1, dst, g.npad);
+        if (paired)
+          for (Step& st : base.steps) st.flags |= mmc::SF_PAIRED;
         TRY(exec_run(ctx, base, s));
         if (hp != ip) CK(mmc::launch_convert(ip, zdst, hp, dst, g, s));
+        if (paired) CK(mmc::launch_pair_layout(zdst, dst, g, 0, s));
       } else if (prec_inner == MMC_BF16) {
         void* v16;
         TRY(scratch(ctx, "sv_v16", field_bytes(g, MMC_BF16), &v16));

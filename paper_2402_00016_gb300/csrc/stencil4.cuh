@@ -43,11 +43,23 @@ using namespace sten;
 
 enum Acc { ACC_NONE = 0, ACC_CODES = 1, ACC_Y = 2, ACC_LEFT = 3 };
 
-// the 12 spin-colour components of a site for RPT right-hand sides
-template <typename S, int R, int RPT>
+// the 12 spin-colour components of a site for RPT right-hand sides; PAIRED: one rhs per
+// lane in the paired-component layout, components 2q and 2q+1 adjacent (one 16-byte load)
+template <typename S, int R, int RPT, bool PAIRED = false>
 __device__ __forceinline__ void load_spinor(const S* p, cx<typename StoreTraits<S>::R> (&v)[12][RPT]) {
+  if constexpr (PAIRED) {
+    static_assert(std::is_same<S, float2>::value && RPT == 1, "paired layout: FP32, one rhs per lane");
 #pragma unroll
-  for (int c = 0; c < 12; ++c) load_rpt<S, RPT>(p + c * R, v[c]);
+    for (int q = 0; q < 6; ++q) {
+      cx<float> pr[2];
+      load_rpt<S, 2>(p + q * 2 * R, pr);
+      v[2 * q][0] = pr[0];
+      v[2 * q + 1][0] = pr[1];
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) load_rpt<S, RPT>(p + c * R, v[c]);
+  }
 }
 
 // upper half-spinor h = P psi of the projector (1 - sg gamma_MU) in the chiral basis
@@ -215,7 +227,7 @@ __device__ __forceinline__ void complete_link(Link<float>& L, bool neg) {
 // LATE: load the next link after the products (18 registers fewer, its latency not hidden).
 // SL: the link of hop D comes from this site's staged links `sl` (8 x 5 pieces).
 // RC: `lk` holds the first two rows of hop D's link; the third is rebuilt here.
-template <typename S, int R, int RPT, int KD, int D, bool LATE, bool SL, bool RC>
+template <typename S, int R, int RPT, int KD, int D, bool LATE, bool SL, bool RC, bool PAIRED>
 __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in, int site, const int4& nf,
                                               const int4& nb, cx<typename StoreTraits<S>::R> (&sp)[12][RPT],
                                               Link<typename StoreTraits<S>::R>& lk, const float4* sl,
@@ -235,11 +247,11 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
   if constexpr (SL) {
     Link<T> lc;
     load_link_shared(sl + D * 5, lc);
-    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
+    load_spinor<S, R, RPT, PAIRED>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
     multiply_add<T, RPT, MU, BWD, SG>(lc, h0, h1, acc);
     fence_arr<T, RPT>(acc);
   } else if constexpr (LATE) {
-    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
+    load_spinor<S, R, RPT, PAIRED>(in + size_t(nsite) * 12 * R, sp);  // after the last hop: the own site
     multiply_add<T, RPT, MU, BWD, SG>(lk, h0, h1, acc);
     fence_arr<T, RPT>(acc);
     if constexpr (D < 7) load_link(p.links, NBWD ? nsite : site, NMU, lk);
@@ -248,14 +260,14 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
     // the time link at t = Lt - 1 (forward from there, backward from t = 0) carries the phase
     const int lsite = BWD ? (MU == 0 ? nb.x : MU == 1 ? nb.y : MU == 2 ? nb.z : nb.w) : site;
     const bool neg = MU == 3 && p.tap && lsite >= (p.Lt - 1) * p.Lx * p.Ly * p.Lz;
-    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);
+    load_spinor<S, R, RPT, PAIRED>(in + size_t(nsite) * 12 * R, sp);
     if constexpr (D < 7) load_link_rows(p.links, NBWD ? nsite : site, NMU, lk);
     complete_link(lc, neg);
     multiply_add<T, RPT, MU, BWD, SG>(lc, h0, h1, acc);
     fence_arr<T, RPT>(acc);
   } else {
     const Link<T> lc = lk;
-    load_spinor<S, R, RPT>(in + size_t(nsite) * 12 * R, sp);
+    load_spinor<S, R, RPT, PAIRED>(in + size_t(nsite) * 12 * R, sp);
     if constexpr (D < 7) load_link(p.links, NBWD ? nsite : site, NMU, lk);
     multiply_add<T, RPT, MU, BWD, SG>(lc, h0, h1, acc);
     fence_arr<T, RPT>(acc);
@@ -264,9 +276,12 @@ __device__ __forceinline__ void hop_pipelined(const step_params& p, const S* in,
 
 // TH: the insertion Theta of the code bilinear when fixed at compile time (0: the
 // identity), -1 when read from p.theta.
-template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH, bool SL, bool RC>
+template <typename S, int R, int RPT, int MINB, int KD, bool AUX, int ACC, int TH, bool SL, bool RC,
+          bool PAIRED = false>
 __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_chunks, int n_items) {
   using T = float;
+  static_assert(!PAIRED || (std::is_same<S, float2>::value && RPT == 1 && ACC == ACC_NONE),
+                "paired layout: FP32 Horner steps (no accumulator, no bilinear)");
   constexpr int L = R / RPT;    // lanes per site
   constexpr int SPP = 128 / L;  // sites per item
   // staged links: [site of the item][hop][piece]; a site's slot is written and read by
@@ -350,7 +365,8 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
     const int pos = (item - rb * n_chunks) * SPP + threadIdx.x / L;
     if (pos >= p.V) continue;
     const size_t rb_off = size_t(rb) * p.V * 12 * R;
-    const S* in = reinterpret_cast<const S*>(p.in) + rb_off + r0;
+    const int lane_off = PAIRED ? 2 * r0 : r0;  // a lane's first element in a site's block
+    const S* in = reinterpret_cast<const S*>(p.in) + rb_off + lane_off;
     const int site = p.order ? __ldg(p.order + pos) : pos;
     const int4 nf = __ldg(reinterpret_cast<const int4*>(p.nbr) + 2 * size_t(site));
     const int4 nb = __ldg(reinterpret_cast<const int4*>(p.nbr) + 2 * size_t(site) + 1);
@@ -379,7 +395,7 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
         cp_async16(smem_addr(sl + q), lsrc + (size_t(src) * 4 + mu) * 5 + k);
       }
     }
-    load_spinor<S, R, RPT>(in + size_t(nf.x) * 12 * R, sp);
+    load_spinor<S, R, RPT, PAIRED>(in + size_t(nf.x) * 12 * R, sp);
     if constexpr (SL) {
       cp_commit_wait_all();
       __syncwarp(site_mask);
@@ -389,16 +405,16 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
       load_link(p.links, site, 0, lk);
     }
     constexpr bool LT = (MINB >= 4) && !SL;
-    hop_pipelined<S, R, RPT, KD, 0, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 1, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 2, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 3, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 4, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 5, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 6, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);
-    hop_pipelined<S, R, RPT, KD, 7, LT, SL, RC>(p, in, site, nf, nb, sp, lk, sl, acc);  // leaves the own spinor in sp
+    hop_pipelined<S, R, RPT, KD, 0, LT, SL, RC, PAIRED>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 1, LT, SL, RC, PAIRED>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 2, LT, SL, RC, PAIRED>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 3, LT, SL, RC, PAIRED>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 4, LT, SL, RC, PAIRED>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 5, LT, SL, RC, PAIRED>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 6, LT, SL, RC, PAIRED>(p, in, site, nf, nb, sp, lk, sl, acc);
+    hop_pipelined<S, R, RPT, KD, 7, LT, SL, RC, PAIRED>(p, in, site, nf, nb, sp, lk, sl, acc);  // leaves the own spinor in sp
 
-    const size_t boff = rb_off + size_t(site) * 12 * R + r0;
+    const size_t boff = rb_off + size_t(site) * 12 * R + lane_off;
     cx<T> si[RPT], so[RPT];
 #pragma unroll
     for (int j = 0; j < RPT; ++j) si[j] = so[j] = cmake(T(0), T(0));
@@ -407,10 +423,7 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
     // one memory latency per component)
     cx<T> yv[ACC == ACC_Y ? 12 : 1][RPT];
     cx<T> axv[AUX ? 12 : 1][RPT];
-    if (AUX) {
-#pragma unroll
-      for (int c = 0; c < 12; ++c) load_rpt<S, RPT>(reinterpret_cast<const S*>(p.aux) + boff + c * R, axv[c]);
-    }
+    if constexpr (AUX) load_spinor<S, R, RPT, PAIRED>(reinterpret_cast<const S*>(p.aux) + boff, axv);
     if (ACC == ACC_Y) {
       const float2* yp = reinterpret_cast<const float2*>(p.y) + boff;
 #pragma unroll
@@ -421,6 +434,7 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
           yv[c][j] = cmake(t.x, t.y);
         }
     }
+    cx<T> vprev = cmake(T(0), T(0));
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       cx<T> vout[RPT];
@@ -430,7 +444,15 @@ __global__ void __launch_bounds__(128, MINB) step4_kernel(step_params p, int n_c
 #pragma unroll
         for (int j = 0; j < RPT; ++j) vout[j] = cfma(cg[j], axv[AUX ? c : 0][j], vout[j]);
       }
-      if (std::is_same<S, __nv_bfloat162>::value && p.salt)
+      if constexpr (PAIRED) {
+        // components 2q and 2q+1 of the lane's rhs are adjacent: one 16-byte store a pair
+        if (c & 1) {
+          const cx<T> pr[2] = {vprev, vout[0]};
+          store_hint<S, 2>(reinterpret_cast<S*>(p.out) + boff + (c >> 1) * 2 * R, pr, ef, pol);
+        } else {
+          vprev = vout[0];
+        }
+      } else if (std::is_same<S, __nv_bfloat162>::value && p.salt)
         store_rpt_sr<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout, srkey, uint32_t(boff + c * R));
       else
         store_hint<S, RPT>(reinterpret_cast<S*>(p.out) + boff + c * R, vout, ef, pol);
@@ -498,7 +520,7 @@ inline int resident_ctas(K kern) {
 
 // Dispatch of one (S, R) family over the epilogue modes (one rhs per lane); false
 // when the flags need another form.  nbx: rows of the bilinear partials (grid bound).
-template <typename S, int R, int MINB, bool SL, bool RC>
+template <typename S, int R, int MINB, bool SL, bool RC, bool PAIRED = false>
 bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err) {
   constexpr int RPT = 1;
   const int f = p.flags;
@@ -510,7 +532,12 @@ bool launch4(const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_
   else if (f & SF_BIL_LEFT) acc = ACC_LEFT;
   if ((f & SF_DAGGER) && (aux || acc != ACC_NONE)) return false;
   void (*kern)(step_params, int, int) = nullptr;
-  if (f & SF_DAGGER) {
+  if constexpr (PAIRED) {
+    // the paired-component layout: the two steps of a Horner chain only
+    if ((f & SF_DAGGER) || acc != ACC_NONE) return false;
+    kern = aux ? step4_kernel<S, R, RPT, MINB, 1, true, ACC_NONE, -1, SL, RC, true>
+               : step4_kernel<S, R, RPT, MINB, 1, false, ACC_NONE, -1, SL, RC, true>;
+  } else if (f & SF_DAGGER) {
     kern = step4_kernel<S, R, RPT, MINB, -1, false, ACC_NONE, -1, SL, RC>;
   } else if (!aux) {
     switch (acc) {

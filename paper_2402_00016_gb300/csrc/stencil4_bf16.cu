@@ -4,7 +4,9 @@
 namespace mmc {
 bool launch_step4_bf16(int R, int minb, const step_params& p, int n_rb, int nbx, cudaStream_t s, cudaError_t* err) {
   // minb 3: 168 registers; 4: 128; 5: 128 with the links staged in shared memory; 6 (special
-  // unitary links): 168 with each link's third row rebuilt from the first two
+  // unitary links): 168 with each link's third row rebuilt from the first two.  No paired-
+  // component layout in BF16.
+  if (p.flags & SF_PAIRED) return false;
   if (R == 16) return minb == 3 ? sten4::launch4<__nv_bfloat162, 16, 3, false, false>(p, n_rb, nbx, s, err)
                      : minb == 6 ? sten4::launch4<__nv_bfloat162, 16, 3, false, true>(p, n_rb, nbx, s, err)
                      : minb == 5 ? sten4::launch4<__nv_bfloat162, 16, 4, true, false>(p, n_rb, nbx, s, err)

@@ -33,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--rmax", type=int, default=16, help="largest rhs block of the field layout (8 or 16)")
     ap.add_argument("--version", type=int, default=0, help="step-kernel version (0: keep the default)")
     ap.add_argument("--hint", type=int, default=-1, help="store hint of version 4 (1: L2 evict-first)")
+    ap.add_argument("--horner-layout", type=int, default=0,
+                    help="--solve: 1 runs the Horner chains in the paired-component layout")
     ap.add_argument("--sweep", default=None,
                     help="JSON list of variants {version, rpt, minb, spc, blocked, hint}: time each in turn")
     ap.add_argument("--solve", type=int, default=0,
@@ -67,6 +69,7 @@ def main(argv=None):
             mmc.mmc_set_step_variant(ctx, prec, 0, 100 + a.version, 0)
         if a.hint >= 0:
             mmc.mmc_set_step_variant(ctx, prec, 0, 400 + a.hint, 0)
+        mmc.mmc_set_horner_layout(ctx, a.horner_layout)
         tuned = mmc.mmc_autotune(ctx, a.nrhs, prec) if a.autotune else None
         if a.deflate > 0:
             vol12 = 12 * int(np.prod(a.dims))

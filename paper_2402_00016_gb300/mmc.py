@@ -132,6 +132,7 @@ _SIGS = {
     "mmc_set_solve_params": (_i, [_vp, _i, _i]),
     "mmc_set_solve_refinement": (_i, [_vp, _d, _i]),
     "mmc_set_gram_schmidt": (_i, [_vp, _i]),
+    "mmc_set_horner_layout": (_i, [_vp, _i]),
     "mmc_autotune": (_i, [_vp, _i, _i, _ip, _dp]),
     "mmc_harmonic_ritz": (_i, [_i, _dp, _i, _dp]),
     "mmc_leja_order": (_i, [_i, _dp, _dp]),
@@ -468,6 +469,10 @@ def mmc_set_solve_refinement(ctx, inner_reduction, inner_cycles):
 
 def mmc_set_gram_schmidt(ctx, passes):
     _check(lib.mmc_set_gram_schmidt(ctx, int(passes)), ctx)
+
+
+def mmc_set_horner_layout(ctx, paired):
+    _check(lib.mmc_set_horner_layout(ctx, int(paired)), ctx)
 
 
 def mmc_set_step_variant(ctx, prec, rpt=0, minb=0, spc=0):

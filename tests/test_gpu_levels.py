@@ -164,11 +164,13 @@ def test_solve_gram_schmidt_passes(mmc, lat, passes):
 def test_solve_8rhs_fourth_form(mmc, lat, minb):
     """Refined solves of 8 vectors (the 8-rhs block class: Horner preconditioner chains
     with the aux operand, M) through the fourth kernel form at 168 registers (minb 3) and
-    at 128 with its links staged in shared memory (minb 5): residual 1e-10 checked with
-    the oracle's M."""
+    at 128 with its links staged in shared memory (minb 5), the Horner chains in the
+    blocked layout (the paired layout runs at 168 registers only): residual 1e-10 checked
+    with the oracle's M."""
     nrhs = 8
     v = {"version": 4, "rpt": 1, "minb": minb, "spc": 64, "blocked": 0, "ns": 0}
     mmc.mmc_set_step_variant_class(lat.ctx, mmc.MMC_F32, 0, v)
+    mmc.mmc_set_horner_layout(lat.ctx, 0)
     try:
         b = mmc.new_field(lat.ctx, nrhs, 0)
         x = mmc.new_field(lat.ctx, nrhs, 0)
@@ -181,6 +183,42 @@ def test_solve_8rhs_fourth_form(mmc, lat, minb):
             r = np.linalg.norm(e - lat.op(xs[j])) / np.linalg.norm(e)
             assert r <= 1.05e-10, (j, r)
     finally:
+        mmc.mmc_set_horner_layout(lat.ctx, 1)
+        mmc.mmc_set_step_variant_class(lat.ctx, mmc.MMC_F32, 0, {"version": 2, "rpt": 1, "minb": 4, "spc": 64,
+                                                                 "blocked": 0, "ns": 0})
+
+
+@pytest.mark.parametrize("minb", [3, 6])
+def test_solve_horner_paired_layout(mmc, lat, minb):
+    """The paired-component layout of the solves' Horner chains (FP32, 8-rhs blocks, fourth
+    kernel form with whole or rebuilt links) against the blocked layout, for a full block of
+    8 vectors and a padded one of 5: the same iteration counts and the same solutions (the
+    arithmetic is the same; a misplaced component would change the preconditioner and with
+    it the iterations), each at residual 1e-10 with the oracle's M."""
+    v = {"version": 4, "rpt": 1, "minb": minb, "spc": 64, "blocked": 0, "ns": 0}
+    mmc.mmc_set_step_variant_class(lat.ctx, mmc.MMC_F32, 0, v)
+    try:
+        hp, _ = mmc.mmc_gmres_poly(lat.ctx, 6)
+        for nrhs in (8, 5):
+            out = []
+            for paired in (0, 1):
+                mmc.mmc_set_horner_layout(lat.ctx, paired)
+                b = mmc.new_field(lat.ctx, nrhs, 0)
+                x = mmc.new_field(lat.ctx, nrhs, 0)
+                mmc.mmc_noise(lat.ctx, 7, 0, mmc.MMC_TAG_NOISE, nrhs, 0, b)
+                its, rel = mmc.mmc_solve(lat.ctx, b, x, nrhs, 1e-10, hp, mmc.MMC_F32, 8, 200)
+                out.append((its, mmc.mmc_unpack(lat.ctx, x, nrhs, 0, lat.V)))
+            assert out[0][0] == out[1][0], (nrhs, out[0][0], out[1][0])
+            for j in range(nrhs):
+                d = np.linalg.norm(out[1][1][j] - out[0][1][j]) / np.linalg.norm(out[0][1][j])
+                assert d < 1e-12, (nrhs, j, d)
+                e = lat.eta(j, 7)
+                r = np.linalg.norm(e - lat.op(out[1][1][j])) / np.linalg.norm(e)
+                assert r <= 1.05e-10, (nrhs, j, r)
+        with pytest.raises(mmc.MMCError):
+            mmc.mmc_set_horner_layout(lat.ctx, 2)
+    finally:
+        mmc.mmc_set_horner_layout(lat.ctx, 1)
         mmc.mmc_set_step_variant_class(lat.ctx, mmc.MMC_F32, 0, {"version": 2, "rpt": 1, "minb": 4, "spc": 64,
                                                                  "blocked": 0, "ns": 0})
 
