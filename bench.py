@@ -134,9 +134,10 @@ TRAFFIC_PER_SITE_RHS = {
     (4, 6, 0, "bilinear", 1): (4.484482e9 + 2.016758e9) / (331776 * 64),  # 306.2 B, third link rows rebuilt
     (4, 6, 1, "bilinear", 1): (4.827532e9 + 2.014122e9) / (331776 * 64),  # 322.2 B, third link rows rebuilt
     (4, 6, 2, "bilinear", 1): (3.473146e9 + 2.012985e9) / (331776 * 64),  # 258.4 B, third link rows rebuilt
-    # the Horner chains of the 8-rhs solves (one launch of the kernel_bench solve mode)
+    # the Horner chains of the 8-rhs solves (one launch of the kernel_bench solve mode; minb 3
+    # in the blocked layout, minb 6 in the paired-component layout the solves use by default)
     (4, 3, 0, "aux", 1): (669.179392e6 + 238.431744e6) / (331776 * 8),  # 341.9 B
-    (4, 6, 0, "aux", 1): (671.003392e6 + 239.062528e6) / (331776 * 8),  # 342.9 B, third link rows rebuilt
+    (4, 6, 0, "aux", 1): (664.114688e6 + 238.064128e6) / (331776 * 8),  # 339.9 B, third link rows rebuilt
 }
 
 
