@@ -44,6 +44,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def time_to_error(var, seconds, noises, eps):
+    """Seconds for the multilevel estimate to reach standard error eps, from one measured step
+    (level l: sample variance var[l], seconds[l] for its noises[l] samples).  Returned: the
+    time at the step's noise proportions, (sum_l seconds_l) (sum_l var_l / N_l) / eps^2 (both
+    factors scale inversely under a common change of every N_l), and the time with the counts
+    re-allocated cost-optimally (N_l proportional to sqrt(var_l / c_l), c_l = seconds_l / N_l,
+    the cost function Sec. 9 names), (sum_l sqrt(var_l c_l))^2 / eps^2."""
+    var_over_n = sum(v / n for v, n in zip(var, noises))
+    fixed = sum(seconds) * var_over_n / eps ** 2
+    sv = sum(np.sqrt(max(v, 0.0) * t / n) for v, t, n in zip(var, seconds, noises))
+    return fixed, sv ** 2 / eps ** 2
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -588,20 +601,18 @@ def main():
                      "per_level_seconds": [r["seconds"] for r in last],
                      "per_level_matvecs": [r["matvecs"] for r in last]},
     }
-    # cost-normalised efficiency: (sum_l T_l) * (sum_l s_l^2 / N_l) is invariant under scaling
-    # every N_l by the same factor, so it gives the time to reach a target error eps as
-    # product / eps^2; the plain FP64 form shares the variances (same estimator)
+    # time to a target error eps at the step's noise proportions and with the counts
+    # re-allocated cost-optimally; the plain FP64 form shares the variances (same estimator)
     eps_target = 0.0005 * float(np.prod(W.dims))
-    var_over_n = sum(r["var_re"] / n for r, (_, _, _, n, _) in zip(last, plan))
+    noises = [n for (_, _, _, n, _) in plan]
+    var_over_n = sum(r["var_re"] / n for r, n in zip(last, noises))
     t_opt = sum(r["seconds"] for r in last)
     line["estimate"]["time_x_var"] = t_opt * var_over_n
     line["estimate"]["eps_target"] = eps_target
-    line["estimate"]["seconds_to_eps"] = t_opt * var_over_n / eps_target ** 2
-    # with the noise counts re-allocated cost-optimally (the cost function Sec. 9 names:
-    # N_l proportional to sqrt(V_l / C_l), C_l the measured seconds per sample) the time to
-    # eps is (sum_l sqrt(V_l C_l))^2 / eps^2
-    sv = sum(np.sqrt(max(r["var_re"], 0.0) * r["seconds"] / n) for r, (_, _, _, n, _) in zip(last, plan))
-    line["estimate"]["seconds_to_eps_cost_optimal"] = sv ** 2 / eps_target ** 2
+    (line["estimate"]["seconds_to_eps"],
+     line["estimate"]["seconds_to_eps_cost_optimal"]) = time_to_error([r["var_re"] for r in last],
+                                                                      [r["seconds"] for r in last], noises,
+                                                                      eps_target)
     if plain:
         t_plain = sum(n * t for (_, _, _, n, _), t in zip(plan, plain["seconds_per_sample_by_level"]))
         plain["time_x_var"] = t_plain * var_over_n
