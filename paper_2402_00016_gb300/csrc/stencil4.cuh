@@ -25,6 +25,12 @@
 // bound by the L1 data pipe, and the link loads are a third of its requests; with 16-rhs
 // blocks a link's loads are shared by twice the rhs.
 //
+// Paired-component layout (PAIRED, FP32, one rhs per lane, no accumulator or bilinear: the
+// Horner chains of the solves): fields [rb][site][c/2][R][c%2], so a lane loads and stores
+// components 2q and 2q+1 of its rhs in one 16-byte access; with 8-rhs blocks a site's lanes
+// then read a whole 128-byte line per instruction instead of half of one, and the launch is
+// no longer bound by the L1 data pipe.
+//
 // Link staging (SL, with 4 resident CTAs per SM): the eight links of each
 // site of an item are copied into shared memory (cp.async, 16-byte pieces, issued by the
 // site's own lanes at the start of the item, together with the first hop's spinor
