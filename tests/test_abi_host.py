@@ -131,3 +131,20 @@ def test_probing_colouring_separates_reach(mmc, dims, reach):
                     assert not np.any(shifted == c), d
                     checked += 1
     assert checked > 0
+
+
+def test_every_context_call_rejects_a_null_context(mmc):
+    """Every entry point that takes a context returns MMC_ERR_ARG for a NULL one (all other
+    arguments zero or NULL) before it touches the device, so none of these calls needs a
+    GPU; mmc_destroy accepts NULL and returns MMC_OK, as its header comment states."""
+    import ctypes
+    checked = 0
+    for name, (res, args) in mmc._SIGS.items():
+        if not args or args[0] is not mmc._vp or res is not mmc._i:
+            continue
+        vals = [0.0 if a is mmc._d else 0 if a in (mmc._i, mmc._u32, mmc._u64, ctypes.c_longlong) else None
+                for a in args]
+        rc = getattr(mmc.lib, name)(*vals)
+        assert rc == (mmc.MMC_OK if name == "mmc_destroy" else mmc.MMC_ERR_ARG), (name, rc)
+        checked += 1
+    assert checked >= 45, checked
