@@ -148,3 +148,20 @@ def test_every_context_call_rejects_a_null_context(mmc):
         assert rc == (mmc.MMC_OK if name == "mmc_destroy" else mmc.MMC_ERR_ARG), (name, rc)
         checked += 1
     assert checked >= 45, checked
+
+
+def test_host_routines_reject_bad_sizes_and_null_buffers(mmc):
+    """The context-free routines (harmonic Ritz values, Leja order, eigenpairs, deflation
+    pairs and condition, probing colouring, context creation) return MMC_ERR_ARG for
+    negative sizes and for NULL buffers with positive sizes, without dereferencing them."""
+    import ctypes
+    checked = 0
+    for name, (res, args) in mmc._SIGS.items():
+        if not args or args[0] is mmc._vp or res is not mmc._i or name == "mmc_rhs_block":
+            continue
+        for size in (-1, 2):
+            vals = [1e-3 if a is mmc._d else size if a in (mmc._i, mmc._u32, mmc._u64, ctypes.c_longlong) else None
+                    for a in args]
+            assert getattr(mmc.lib, name)(*vals) == mmc.MMC_ERR_ARG, (name, size)
+        checked += 1
+    assert checked >= 7, checked
